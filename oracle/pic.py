@@ -1,0 +1,258 @@
+"""One time step of the orbit-discrete-gradient CN potential PIC method (test infrastructure only).
+
+Follows Algorithm 1 ("Picard iteration for the orbit-discrete-gradient CN potential PIC
+step") in the paper's order, with the orbit push of §4.4 (Eq. (orbit-push)), the
+initial data of §5.4 and the diagnostics of §5.1-§5.3.
+
+Readings of points the paper leaves open (each is listed in the design notes):
+
+* History velocity at the first step: v^{-1} := v^0, so the first guess is v^0.
+* Picard norms: e_v = ||v^{n+1,p+1} - v^{n+1,p}||_2 / ||v^{n+1,p+1}||_2 over all
+  particles and components; e_J = ||J^p - J^{p-1}||_2 / (||J^p||_2 + J_scale) with
+  J_scale = sqrt(N_cells) * sum_i |q_i| |v_i^n| / |Omega| (a floor, because the
+  paired beams start with J ~ 0, §5.4); e_J is not defined at p = 0, so p = 0
+  never converges.  Converged when both are <= tau.
+* Final consistency sweep (§5.4): after convergence at iterate p, one more iteration
+  is run from v^{n+1,p+1}; its current, fields, orbit integrals and particle state
+  are the accepted step and feed the diagnostics.
+* Not converged after p = 0..p_max: the step is reported as not converged (the
+  caller keeps the old state).
+* Initial charge: rho_g = sum_i q_i S_g(x_i) / dV plus the ion background, with the
+  null modes of Delta_h (the mean and the checkerboards) removed; Poisson's 1/eps0 is
+  read as sigma1.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+from . import mesh, orbit
+
+CHUNK = 32768
+
+
+@dataclass
+class Config:
+    n: tuple
+    L: tuple
+    dt: float
+    kappa: float = 1.0
+    sigma1: float = 1.0
+    sigma2: float = 1.0
+    picard_tol: float = 1e-14
+    picard_max: int = 16
+    split: bool = True
+    quadrature: str = "closed"   # "closed" (Appendices A/B) or "gauss" (§4.7 split Gauss rule)
+    nq: int = 16
+    n0: float = 1.0              # ion background density (§5.4)
+
+    def grid(self):
+        return mesh.Grid(self.n, self.L)
+
+
+@dataclass
+class State:
+    xi: np.ndarray      # (np, 3) position in cell units, wrapped to [0, n)
+    v: np.ndarray       # (np, 3) v^n
+    P: np.ndarray       # (np, 3) canonical momentum P^n
+    vprev: np.ndarray   # (np, 3) history velocity v^{n-1}
+    q: float
+    m: float
+    phi: np.ndarray
+    psi: np.ndarray
+    A: np.ndarray       # (3, nx, ny, nz)
+    U: np.ndarray
+    rho: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+
+def wrap_cells(xi, n):
+    """Wrap cell-unit positions onto [0, n_a) per axis."""
+    nn = np.asarray(n, dtype=np.float64)
+    w = xi - nn * np.floor(xi / nn)
+    return np.where(w >= nn, w - nn, w)
+
+
+def orbit_weights(xi0, beta, cfg, grid, with_gradient=True):
+    if cfg.quadrature == "closed":
+        return orbit.closed_form_weights(xi0, beta, grid, cfg.split, with_gradient)
+    if cfg.quadrature == "gauss":
+        return orbit.gauss_weights(xi0, beta, grid, cfg.nq, cfg.split)
+    raise ValueError(cfg.quadrature)
+
+
+def _chunks(npart):
+    for a in range(0, npart, CHUNK):
+        yield slice(a, min(a + CHUNK, npart))
+
+
+# --- Initial data (§5.4) ---------------------------------------------------------------
+
+def point_deposit(xi, q, grid):
+    """rho_e,g = sum_i q S_g(x_i) / dV (Eq. (source-moments), with the 1/dV of Eq. (orbit-current))."""
+    rho = np.zeros(grid.n)
+    for sl in _chunks(xi.shape[0]):
+        nodes, S, _ = orbit.point_shape(xi[sl], grid)
+        rho += np.bincount(orbit.flat_index(nodes, grid.n).ravel(), weights=(q * S).ravel() / grid.dV,
+                           minlength=grid.ncell).reshape(grid.n)
+    return rho
+
+
+def init(x, v, q, m, cfg):
+    """Initial state from particle positions x (physical units) and velocities v (§5.4)."""
+    grid = cfg.grid()
+    H = np.asarray(grid.H)
+    xi = wrap_cells(np.asarray(x, dtype=np.float64) / H, grid.n)
+    v = np.array(v, dtype=np.float64)
+    rho_e = point_deposit(xi, q, grid)
+    rho = rho_e + cfg.n0
+    rho = rho - np.mean(rho)
+    rho = mesh.project_out_null(rho, grid)
+    phi = mesh.poisson(rho, cfg.sigma1, grid)
+    A = np.zeros((3,) + grid.n)
+    P = m * v + q * orbit.point_gather(A, xi, grid).T
+    return State(xi=xi, v=v, P=P, vprev=v.copy(), q=float(q), m=float(m), phi=phi,
+                 psi=np.zeros(grid.n), A=A, U=np.zeros((3,) + grid.n), rho=rho)
+
+
+# --- Algorithm 1 ---------------------------------------------------------------------
+
+def picard_iteration(st, v_it, cfg, grid, diagnostics=False):
+    """One pass of the Algorithm 1 loop body for the end-of-step velocity iterate ``v_it``."""
+    H = np.asarray(grid.H)
+    dt = cfg.dt
+    vbar = 0.5 * (v_it + st.v)                       # orbit implied by the iterate
+    beta = dt * vbar / H                             # unwrapped displacement in cell units
+    # orbit current (Eq. (orbit-current)), split-path weights
+    J = np.zeros((3,) + grid.n)
+    for sl in _chunks(st.xi.shape[0]):
+        ow = orbit_weights(st.xi[sl], beta[sl], cfg, grid, with_gradient=False)
+        J += orbit.deposit(st.q * vbar[sl], ow, grid)
+    # continuity (Eq. (cn-continuity)) and CN potential solve (Eq. (cn-field-update))
+    rho1 = mesh.continuity(st.rho, J, dt, grid)
+    rho_half = 0.5 * (rho1 + st.rho)
+    phi1, psi1, A1, U1 = mesh.cn_fields(st.phi, st.psi, st.A, st.U, rho_half, J, dt,
+                                        cfg.kappa, cfg.sigma1, cfg.sigma2, grid)
+    # midpoint mesh fields
+    gphi_half = mesh.grad(0.5 * (phi1 + st.phi), grid)
+    U_half = 0.5 * (U1 + st.U)
+    npart = st.xi.shape[0]
+    P1 = np.empty((npart, 3))
+    xi1 = np.empty((npart, 3))
+    v_new = np.empty((npart, 3))
+    diag = {"RA": np.empty((npart, 3)), "pu": np.empty(npart), "pwork": 0.0} if diagnostics else None
+    for sl in _chunks(npart):
+        ow = orbit_weights(st.xi[sl], beta[sl], cfg, grid)
+        gphibar = orbit.gather(gphi_half, ow).T                     # (np, 3)  Eq. (gphibar-definition)
+        DA = orbit.orbit_gradient(st.A, A1, ow)                     # (np, l, j)  Eq. (DA-def)
+        DAT_vbar = np.einsum("ilj,il->ij", DA, vbar[sl])            # ((D A)^T vbar)_j
+        P1[sl] = st.P[sl] + dt * (-st.q * gphibar + st.q * DAT_vbar)   # Eq. (orbit-P-update)
+        xend = st.xi[sl] + beta[sl]                                  # Eq. (orbit-x-update), unwrapped
+        xi1[sl] = wrap_cells(xend, grid.n)
+        A_end = orbit.point_gather(A1, xi1[sl], grid).T              # A_h^{n+1}(x^{n+1})
+        v_new[sl] = (P1[sl] - st.q * A_end) / st.m                   # Eq. (orbit-v-update)
+        if diagnostics:
+            Ubar = orbit.gather(U_half, ow).T                        # Eq. (Ubar-def)
+            A_start = orbit.point_gather(st.A, st.xi[sl], grid).T
+            DA_vbar = np.einsum("ilj,ij->il", DA, vbar[sl])          # (D A) vbar
+            diag["RA"][sl] = A_end - A_start - dt * (Ubar + DA_vbar)     # Eq. (RA-test)
+            diag["pu"][sl] = np.sum(ow.w, axis=1) - 1.0                  # Appendix A partition of unity
+            Ebar = -gphibar - Ubar                                       # Eq. (orbit-E-gather)
+            diag["pwork"] += float(np.sum(st.q * vbar[sl] * Ebar))
+    out = dict(J=J, rho=rho1, phi=phi1, psi=psi1, A=A1, U=U1, P=P1, xi=xi1, v_new=v_new, vbar=vbar)
+    if diagnostics:
+        E_half = -gphi_half - U_half
+        diag["mwork"] = float(np.sum(J * E_half) * grid.dV)               # sum_g J . E dV
+        out["diag"] = diag
+    return out
+
+
+def j_scale(st, grid):
+    return np.sqrt(grid.ncell) * abs(st.q) * np.sum(np.linalg.norm(st.v, axis=1)) / grid.volume
+
+
+def step(st, cfg):
+    """Advance one time step (Algorithm 1 plus the final consistency sweep of §5.4).
+
+    Returns (new_state, info).  ``info['converged']`` is False when p_max was reached;
+    the caller then keeps ``st``.
+    """
+    grid = cfg.grid()
+    v_it = 2.0 * st.v - st.vprev                     # extrapolated initial iterate
+    J_prev = None
+    jsc = j_scale(st, grid)
+    hist = []
+    converged = False
+    for p in range(cfg.picard_max + 1):
+        it = picard_iteration(st, v_it, cfg, grid)
+        e_v = np.linalg.norm(it["v_new"] - v_it) / np.linalg.norm(it["v_new"])
+        e_J = np.inf if J_prev is None else np.linalg.norm(it["J"] - J_prev) / (np.linalg.norm(it["J"]) + jsc)
+        hist.append((float(e_v), float(e_J)))
+        if e_v <= cfg.picard_tol and e_J <= cfg.picard_tol:
+            converged = True
+            break
+        v_it = it["v_new"]
+        J_prev = it["J"]
+    info = {"converged": converged, "iterations": len(hist), "errors": hist}
+    if not converged:
+        return st, info
+    fin = picard_iteration(st, it["v_new"], cfg, grid, diagnostics=True)
+    new = State(xi=fin["xi"], v=fin["v_new"], P=fin["P"], vprev=st.v.copy(), q=st.q, m=st.m,
+                phi=fin["phi"], psi=fin["psi"], A=fin["A"], U=fin["U"], rho=fin["rho"])
+    K0, W0 = energy(st, cfg)
+    K1, W1 = energy(new, cfg)
+    d = fin["diag"]
+    info.update(
+        K0=K0, W0=W0, K1=K1, W1=W1,
+        mesh_work=d["mwork"], particle_work=d["pwork"],
+        R_field=W1 - W0 + cfg.dt * d["mwork"],                  # Eq. (R-field)
+        R_particle=K1 - K0 - cfg.dt * d["pwork"],               # Eq. (R-particle)
+        R_total=(K1 + W1) - (K0 + W0),                          # Eq. (R-total)
+        RA=d["RA"], partition_of_unity=d["pu"],
+        continuity=new.rho - st.rho + cfg.dt * mesh.div(fin["J"], grid),
+        J=fin["J"], vbar=fin["vbar"],
+    )
+    return new, info
+
+
+# --- Energies and mesh diagnostics (§4.1, §5.1) ----------------------------------------
+
+def kinetic_energy(st):
+    """K = sum_i m_i |v_i|^2 / 2 (Eq. (particle-energy))."""
+    return float(0.5 * st.m * np.sum(st.v * st.v))
+
+
+def energy(st, cfg):
+    grid = cfg.grid()
+    return kinetic_energy(st), mesh.field_energy(st.phi, st.U, st.A, cfg.sigma1, cfg.sigma2, grid)
+
+
+def mesh_diagnostics(st, cfg):
+    grid = cfg.grid()
+    return {
+        "gauge": mesh.gauge_residual(st.psi, st.A, cfg.kappa, grid),
+        "gauss": mesh.gauss_residual(st.phi, st.U, st.rho, cfg.sigma1, grid),
+    }
+
+
+def positions(st, cfg):
+    """Physical positions x = xi * H."""
+    return st.xi * np.asarray(cfg.grid().H)
+
+
+def run(st, cfg, nsteps):
+    """Advance nsteps; stops early (returning the last good state) if a step fails to converge."""
+    infos = []
+    for _ in range(nsteps):
+        new, info = step(st, cfg)
+        infos.append(info)
+        if not info["converged"]:
+            break
+        st = new
+    return st, infos
+
+
+__all__ = ["Config", "State", "init", "step", "run", "energy", "kinetic_energy",
+           "mesh_diagnostics", "picard_iteration", "wrap_cells", "positions", "replace"]

@@ -1,0 +1,138 @@
+"""Cold two-stream initial particles (counter-based, seeded, platform independent).
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) evaluated on a counter: draw ``c`` of
+stream ``seed`` is ``mix(seed * 0x9E3779B97F4A7C15 + (c + 1) * 0xD1B54A32D192ED03)``
+with the SplitMix64 finaliser ``mix``; the top 53 bits give a uniform double in
+[0, 1).  Gaussians use the Box--Muller transform.  Everything is numpy uint64/float64
+arithmetic, so x86 and Arm hosts produce identical arrays.
+
+Workload recipe (the same physics as the paper's §5.4 cold two-stream test, in the
+box and sizes of the benchmark workloads): a periodic cube of side 2 pi / 3 (so the
+fundamental wavenumber is k1 = 3 and k1 v0 = 0.6 at v0 = 0.2), immobile neutralising
+ions of density n0 = 1, two electron beams drifting at +-v0 along x with identical
+positions, positions uniform in the box then displaced in x by eps sin(k1 x), an
+optional Gaussian thermal spread, q = -n0 |Omega| / N_p and m = |q| (so q/m = -1).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_STEP = np.uint64(0xD1B54A32D192ED03)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z):
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64_uniform(seed, counters):
+    """Uniform doubles in [0, 1) for the given counters of stream ``seed``."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) * _GOLDEN + (c + np.uint64(1)) * _STEP
+        z = _mix(z)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def _normals(seed, base, count):
+    """``count`` standard normals from counters base .. base + 2*ceil(count/2) (Box--Muller)."""
+    npair = (count + 1) // 2
+    u1 = splitmix64_uniform(seed, base + 2 * np.arange(npair, dtype=np.uint64))
+    u2 = splitmix64_uniform(seed, base + 2 * np.arange(npair, dtype=np.uint64) + np.uint64(1))
+    rad = np.sqrt(-2.0 * np.log1p(-u1))          # 1 - u1 in (0, 1]
+    z = np.concatenate([rad * np.cos(2 * np.pi * u2), rad * np.sin(2 * np.pi * u2)])
+    return z[:count]
+
+
+def random_twostream(n, L, per_beam_per_cell, v0, eps, vth, seed, n0=1.0):
+    """Two beams at +-v0 (x) with identical uniform random positions, x displaced by eps sin(k1 x).
+
+    Returns (x (Np, 3), v (Np, 3), q, m); beam + is the first half, beam - the second.
+    """
+    n = tuple(int(a) for a in n)
+    L = tuple(float(a) for a in L)
+    npairs = per_beam_per_cell * n[0] * n[1] * n[2]
+    idx = np.arange(npairs, dtype=np.uint64)
+    pos = np.stack([splitmix64_uniform(seed, 3 * idx + np.uint64(a)) * L[a] for a in range(3)], axis=1)
+    k1 = 2.0 * np.pi / L[0]
+    pos[:, 0] = pos[:, 0] + eps * np.sin(k1 * pos[:, 0])
+    pos[:, 0] = np.mod(pos[:, 0], L[0])
+    pos[:, 0] = np.where(pos[:, 0] >= L[0], 0.0, pos[:, 0])
+    x = np.concatenate([pos, pos])
+    v = np.zeros((2 * npairs, 3))
+    v[:npairs, 0] = v0
+    v[npairs:, 0] = -v0
+    if vth > 0:
+        base = np.uint64(3 * npairs)
+        v += vth * _normals(seed, base, 6 * npairs).reshape(2 * npairs, 3)
+    volume = L[0] * L[1] * L[2]
+    q = -n0 * volume / (2 * npairs)
+    return x, v, q, abs(q)
+
+
+def lattice_twostream(n, L, pairs_per_cell, v0, eps, mode=1, n0=1.0):
+    """The paper's quiet start (§5.4): a cell-centred x lattice repeated in every y-z cell.
+
+    Per cell, ``pairs_per_cell`` positions x = (ix + (j + 1/2)/pairs_per_cell) Hx at the
+    y-z cell centre; both beams share them; v_x = +-v0 + eps sin(k x), k = 2 pi mode / Lx.
+    """
+    n = tuple(int(a) for a in n)
+    L = tuple(float(a) for a in L)
+    H = [L[a] / n[a] for a in range(3)]
+    ix, iy, iz, j = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]),
+                                np.arange(pairs_per_cell), indexing="ij")
+    pos = np.stack([(ix + (j + 0.5) / pairs_per_cell) * H[0], (iy + 0.5) * H[1], (iz + 0.5) * H[2]],
+                   axis=-1).reshape(-1, 3)
+    npairs = pos.shape[0]
+    k = 2.0 * np.pi * mode / L[0]
+    pert = eps * np.sin(k * pos[:, 0])
+    x = np.concatenate([pos, pos])
+    v = np.zeros((2 * npairs, 3))
+    v[:npairs, 0] = v0 + pert
+    v[npairs:, 0] = -v0 + pert
+    volume = L[0] * L[1] * L[2]
+    q = -n0 * volume / (2 * npairs)
+    return x, v, q, abs(q)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: tuple
+    per_beam_per_cell: int
+    v0: float
+    eps: float
+    vth: float
+    dt: float
+    steps: int
+    picard_tol: float
+    seed: int
+
+    @property
+    def L(self):
+        side = 2.0 * np.pi / 3.0
+        return (side, side, side)
+
+    @property
+    def n_particles(self):
+        return 2 * self.per_beam_per_cell * self.n[0] * self.n[1] * self.n[2]
+
+
+# Seeds follow 1000 + 100 * workload + run.
+WORKLOADS = {
+    "twostream-8c-8k": Workload("twostream-8c-8k", (8, 8, 8), 8, 0.2, 1e-3, 0.0, 0.1, 50, 1e-14, 1100),
+    "twostream-32c-2M": Workload("twostream-32c-2M", (32, 32, 32), 32, 0.2, 1e-3, 1e-4, 0.1, 500, 1e-13, 1200),
+    "twostream-128c-134M": Workload("twostream-128c-134M", (128, 128, 128), 32, 0.2, 1e-3, 1e-4, 0.1, 200, 1e-13, 1300),
+}
+
+
+def workload_particles(w: Workload, run: int = 0):
+    return random_twostream(w.n, w.L, w.per_beam_per_cell, w.v0, w.eps, w.vth, w.seed + run)

@@ -1,0 +1,208 @@
+"""Pins of the oracle's whole time step (Algorithm 1) against what the paper proves and measures.
+
+* Theorem "discrete total energy conservation": R_total at roundoff for the converged
+  split-orbit step; R_field and R_particle (Eq. (R-field), Eq. (R-particle)) at solver
+  tolerance; R_A (Eq. (RA-test)) at roundoff; partition of unity; exact continuity;
+  gauge and Gauss residuals (§5.1) at roundoff.
+* The unsplit comparison run (§5.4): G_h, R_h still at roundoff, R_A and the energy
+  defect not (figures of §5.4).
+* Split Gauss quadrature reproduces the closed-form step (§5.4, "the answer is identical").
+* Cold two-stream linear growth (§5.4 physics) against the cold symmetric two-beam
+  dispersion relation 1 = (w_p^2/2)[(w - k v0)^-2 + (w + k v0)^-2], started on its
+  growing eigenmode.
+* Planted mistakes: pushing with (D A) instead of (D A)^T must break energy
+  conservation.
+"""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import mesh, orbit, pic
+
+
+def _c1_small(per_beam=8, n=(8, 8, 8), tol=1e-14):
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.random_twostream(n, w.L, per_beam, w.v0, w.eps, 0.0, w.seed)
+    cfg = pic.Config(n=n, L=w.L, dt=w.dt, picard_tol=tol)
+    return pic.init(x, v, q, m, cfg), cfg
+
+
+def _check_step_identities(info, new, cfg, E0):
+    grid = cfg.grid()
+    assert info["converged"]
+    assert abs(info["R_total"]) <= 1e-14 * E0
+    assert abs(info["R_field"]) <= 1e-14 * E0
+    assert abs(info["R_particle"]) <= 1e-13 * E0
+    assert np.abs(info["RA"]).max() <= 1e-15
+    assert np.abs(info["partition_of_unity"]).max() <= 8 * np.finfo(float).eps
+    assert np.abs(info["continuity"]).max() <= 1e-14 * max(1.0, np.abs(new.rho).max())
+    md = pic.mesh_diagnostics(new, cfg)
+    assert np.abs(md["gauge"]).max() <= 1e-12
+    assert np.abs(md["gauss"]).max() <= 1e-12 * max(1.0, np.abs(new.rho).max())
+    # the power identity of Eq. (power-test)
+    assert abs(info["particle_work"] - info["mesh_work"]) <= 1e-13 * max(1e-3, abs(info["mesh_work"]))
+
+
+def test_split_step_conserves_energy_and_constraints():
+    st, cfg = _c1_small()
+    K, W = pic.energy(st, cfg)
+    E0 = K + W
+    for _ in range(4):
+        new, info = pic.step(st, cfg)
+        _check_step_identities(info, new, cfg, E0)
+        st = new
+    K1, W1 = pic.energy(st, cfg)
+    assert abs((K1 + W1) - E0) <= 1e-14 * E0
+
+
+def test_initial_state_satisfies_constraints():
+    st, cfg = _c1_small()
+    md = pic.mesh_diagnostics(st, cfg)
+    assert np.abs(md["gauge"]).max() == 0.0
+    assert np.abs(md["gauss"]).max() <= 1e-12
+    assert abs(np.mean(st.rho)) <= 1e-15
+    np.testing.assert_array_equal(st.vprev, st.v)
+
+
+def test_split_gauss_step_equals_closed_form_step():
+    st, cfg = _c1_small(per_beam=2)
+    cfg_g = pic.Config(n=cfg.n, L=cfg.L, dt=cfg.dt, picard_tol=cfg.picard_tol, quadrature="gauss", nq=2)
+    a, ia = pic.step(st, cfg)
+    b, ib = pic.step(st, cfg_g)
+    assert ia["converged"] and ib["converged"]
+    np.testing.assert_allclose(b.v, a.v, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(b.P, a.P, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(b.phi, a.phi, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(b.A, a.A, rtol=0, atol=1e-15)
+
+
+def test_unsplit_run_keeps_constraints_but_breaks_chain_rule():
+    st, cfg = _c1_small(per_beam=2)
+    cfg_u = pic.Config(n=cfg.n, L=cfg.L, dt=cfg.dt, picard_tol=1e-13, quadrature="gauss", nq=16, split=False)
+    K, W = pic.energy(st, cfg)
+    E0 = K + W
+    ra_split, ra_unsplit, rp_unsplit = 0.0, 0.0, 0.0
+    s1, s2 = st, st
+    for _ in range(3):
+        s1, i1 = pic.step(s1, cfg)
+        s2, i2 = pic.step(s2, cfg_u)
+        assert i1["converged"] and i2["converged"]
+        ra_split = max(ra_split, np.abs(i1["RA"]).max())
+        ra_unsplit = max(ra_unsplit, np.abs(i2["RA"]).max())
+        rp_unsplit = max(rp_unsplit, abs(i2["R_particle"]))
+        md = pic.mesh_diagnostics(s2, cfg_u)
+        assert np.abs(md["gauge"]).max() <= 1e-12
+        assert np.abs(md["gauss"]).max() <= 1e-11
+        assert abs(i2["R_field"]) <= 1e-14 * E0
+    assert ra_unsplit > 1e6 * max(ra_split, 1e-22)
+    assert rp_unsplit > 1e-12 * E0
+
+
+def test_nonconvergence_keeps_state():
+    st, cfg = _c1_small(per_beam=2)
+    cfg1 = pic.Config(n=cfg.n, L=cfg.L, dt=cfg.dt, picard_tol=1e-14, picard_max=1)
+    new, info = pic.step(st, cfg1)
+    assert not info["converged"]
+    assert new is st
+
+
+def _eigenmode_start(nx=16, pairs=16, E0=1e-4, v0=0.2):
+    """Lattice start (§5.4) displaced and kicked along the growing eigenmode of the cold beams."""
+    L = (2 * np.pi / 3, 0.5, 0.5)
+    x, v, q, m = pi.lattice_twostream((nx, 2, 2), L, pairs, v0, 0.0, mode=1)
+    k = 2 * np.pi / L[0]
+    a = k * v0
+    gam = np.sqrt(-(2 * a * a + 1 - np.sqrt(1 + 8 * a * a)) / 2)
+    npair = x.shape[0] // 2
+    for s, sl in [(1, slice(0, npair)), (-1, slice(npair, None))]:
+        om = 1j * gam
+        dv = -1j * E0 / (om - s * a)                 # cold-fluid velocity response (q/m = -1)
+        dn = (k * 0.5) * dv / (om - s * a)           # beam density response (n0/2 per beam)
+        disp = 1j * dn / (k * 0.5)                   # displacement giving that density
+        x0 = x[sl, 0].copy()
+        x[sl, 0] = np.mod(x0 + np.real(disp * np.exp(1j * k * x0)), L[0])
+        v[sl, 0] += np.real(dv * np.exp(1j * k * x0))
+    cfg = pic.Config(n=(nx, 2, 2), L=L, dt=0.1, picard_tol=1e-12)
+    return pic.init(x, v, q, m, cfg), cfg, gam
+
+
+def test_two_stream_linear_growth_matches_dispersion_relation():
+    st, cfg, gam = _eigenmode_start()
+    amps = []
+    for _ in range(40):
+        st, info = pic.step(st, cfg)
+        assert info["converged"]
+        amps.append(abs(np.fft.fft(st.rho.mean(axis=(1, 2)))[1]))
+    t = 0.1 * np.arange(1, 41)
+    sel = t >= 0.5
+    g = np.polyfit(t[sel], np.log(np.asarray(amps)[sel]), 1)[0]
+    assert abs(g - gam) <= 0.02 * gam, (g, gam)
+
+
+def _transverse_A_start(amp=0.05, nx=8, pairs=4):
+    """Lattice start (§5.4) whose fields depend on x only, with a transverse A_y(x) seeded.
+
+    Every y-z cell holds the same particles, so deposits, and hence all fields, stay
+    independent of y and z.  A_y(x) = amp sin(k x) is divergence free, so the Lorenz
+    gauge still holds with psi = 0; P = m v + q A_h(x) keeps the canonical relation.
+    """
+    L = (2 * np.pi / 3, 0.6, 0.6)
+    n = (nx, 4, 4)
+    x, v, q, m = pi.lattice_twostream(n, L, pairs, 0.2, 1e-3, mode=1)
+    cfg = pic.Config(n=n, L=L, dt=0.1, picard_tol=1e-13)
+    st = pic.init(x, v, q, m, cfg)
+    grid = cfg.grid()
+    xs = np.arange(n[0]) * grid.H[0]
+    A = np.zeros((3,) + n)
+    A[1] = (amp * np.sin(2 * np.pi * xs / L[0]))[:, None, None]
+    A[2] = (0.5 * amp * np.cos(4 * np.pi * xs / L[0]))[:, None, None]
+    st = pic.replace(st, A=A)
+    st = pic.replace(st, P=st.m * st.v + st.q * orbit.point_gather(A, st.xi, grid).T)
+    return st, cfg
+
+
+def test_split_step_conserves_energy_with_strong_vector_potential():
+    st, cfg = _transverse_A_start()
+    assert np.abs(pic.mesh_diagnostics(st, cfg)["gauge"]).max() < 1e-12
+    K, W = pic.energy(st, cfg)
+    E0 = K + W
+    for _ in range(3):
+        new, info = pic.step(st, cfg)
+        assert info["converged"]
+        assert abs(info["R_total"]) <= 1e-13 * E0
+        assert abs(info["R_particle"]) <= 1e-12 * E0
+        assert np.abs(info["RA"]).max() <= 1e-14
+        md = pic.mesh_diagnostics(new, cfg)
+        assert np.abs(md["gauge"]).max() <= 1e-11
+        st = new
+
+
+def test_canonical_momentum_conserved_along_symmetry_directions():
+    """With fields independent of y and z, Eq. (orbit-P-update) leaves P_y and P_z unchanged.
+
+    (D_i A)^T vbar has j-th entry sum_l int A_l(s) d_j S dot vbar_l, and sum_g A_g d_y S_g
+    vanishes when A_g does not depend on y (partition of unity along y); the mesh gradient
+    of phi has no y or z part either.  This mirrors Eq. (model-Pdot): P_j is conserved
+    when the potentials do not depend on x_j.
+    """
+    st, cfg = _transverse_A_start()
+    P0 = st.P.copy()
+    for _ in range(3):
+        st, info = pic.step(st, cfg)
+        assert info["converged"]
+    assert np.abs(st.P[:, 1:] - P0[:, 1:]).max() <= 1e-18
+    assert np.abs(st.P[:, 0] - P0[:, 0]).max() > 1e-9       # the x momentum does change
+
+
+def test_planted_transposed_push_breaks_momentum_symmetry(monkeypatch):
+    """Pushing with (D A) vbar instead of (D A)^T vbar conserves energy (v.Mv = v.M^T v,
+    Eq. (DA-cancellation)) but not the symmetry-direction canonical momentum: the pin above
+    must catch it."""
+    st, cfg = _transverse_A_start()
+    orig = orbit.orbit_gradient
+    monkeypatch.setattr(orbit, "orbit_gradient", lambda An, An1, ow: orig(An, An1, ow).transpose(0, 2, 1))
+    new, info = pic.step(st, cfg)
+    monkeypatch.setattr(orbit, "orbit_gradient", orig)
+    assert info["converged"]
+    assert np.abs(new.P[:, 1:] - st.P[:, 1:]).max() > 1e-10
