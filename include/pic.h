@@ -1,0 +1,213 @@
+/*
+ * pic.h -- C-ABI of the GB300 (sm_103a) energy-conserving unstaggered potential PIC step.
+ *
+ * The library advances the paper's method (arXiv 2606.15035, "An Energy-Conserving
+ * Unstaggered Electromagnetic-Potential Particle-in-Cell Method, Part I"): a periodic box,
+ * node-collocated potentials (phi, psi = d_t phi, A, U = d_t A) and charge rho, and
+ * electron macro-particles carried by position x, velocity v and canonical momentum
+ * P = m v + q A_h(x).  One call to pic_step runs Algorithm 1 ("Picard iteration for the
+ * orbit-discrete-gradient CN potential PIC step") per time step:
+ *   orbit-averaged current J^{n+1/2} (§4.2, Eq. (orbit-current)) ->
+ *   charge from continuity (§3.2, Eq. (cn-continuity)) ->
+ *   Crank--Nicolson potential update (§3.2, Eq. (cn-field-update)) ->
+ *   orbit gather of grad phi and the orbit-discrete gradient D_i A (§4.3-§4.4,
+ *   Eq. (gphibar-definition), Eq. (DA-def), Appendices A/B) ->
+ *   canonical-momentum push (§4.4, Eq. (orbit-push)),
+ * repeated until the current and velocity fixed-point errors fall below tolerance,
+ * followed by one final consistency sweep (§5.4) whose state is committed.
+ *
+ * Conventions shared by every entry point
+ *   - Mesh arrays are float64, x-fastest: node (ix, iy, iz) is element
+ *     ix + nx * (iy + ny * iz).  Vector mesh fields are component-major: component c of
+ *     node g is element c * ncell + g.
+ *   - Particle arrays are float64 structure-of-arrays: component c of particle i is
+ *     element c * np + i.  Positions are physical (in [0, L) after wrapping).
+ *   - Pointers passed in are borrowed for the duration of the call only.  A flag
+ *     `on_device` says whether they are device (1) or host (0) addresses.
+ *   - All device work runs on the CUDA stream given to pic_init, in order.  Calls that
+ *     return host values synchronise that stream.
+ *   - Every call returns a pic_status; none aborts, traps or exits.  After an error,
+ *     pic_last_error(ctx) gives a one-line reason.  A pic_step that fails leaves the
+ *     state at the last committed step.
+ *   - Spatial operators are the periodic second-order central difference D_a and the
+ *     Laplacian Delta_h = sum_a D_a D_a, which give the identities the paper's theorems
+ *     use (§3.3, §4.6).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,             /* invalid argument or configuration */
+    PIC_ERR_OOM = 2,             /* device allocation failed */
+    PIC_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    PIC_ERR_NO_CONVERGENCE = 4,  /* Picard reached picard_max without meeting picard_tol */
+    PIC_ERR_NONFINITE = 5,       /* a non-finite residual or velocity appeared */
+    PIC_ERR_SEGMENTS = 6,        /* an orbit crossed more knots in one step than supported */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };
+enum { PIC_QUAD_CLOSED = 0, PIC_QUAD_GAUSS = 1 };
+
+/* Run configuration.  Fill with pic_config_default, then override. */
+typedef struct {
+    int32_t n[3];                 /* mesh nodes per axis (periodic) */
+    double L[3];                  /* box lengths; H_a = L_a / n_a */
+    double dt;                    /* time step */
+    double kappa, sigma1, sigma2; /* light speed and source coefficients (§2.1); sigma1 = kappa^2 sigma2 */
+    double n0;                    /* immobile ion background density (§5.4) */
+    double picard_tol;            /* tau: both fixed-point errors must be <= tau (Algorithm 1) */
+    int32_t picard_max;           /* p_max: iterations p = 0 .. p_max */
+    int32_t split_orbit_at_knots; /* 1: split at every crossed knot (conservative); 0: unsplit (Gauss only) */
+    int32_t quadrature;           /* PIC_QUAD_CLOSED (Appendices A/B) or PIC_QUAD_GAUSS (§4.7) */
+    int32_t nq;                   /* Gauss points per piece when quadrature = PIC_QUAD_GAUSS (1..16) */
+    int32_t precision;            /* PIC_FP64 (mixed precision is selected by this field as well) */
+    int32_t sort_every;           /* re-sort particles by cell every k steps (0: never) */
+    int32_t diagnostics;          /* 1: accumulate the §5.1-§5.3 diagnostics during each step */
+    int32_t accept_unconverged;   /* 1: commit a step that hit p_max (Algorithm 1 as printed) */
+    int32_t picard_accel;         /* 1: particles whose orbit crosses a knot on an axis where they
+                                     move < 0.1 cells get a particle-local solve of v = G_i(v)
+                                     with the iteration's fields fixed (an accelerated fixed point,
+                                     §4.8); all others, and every particle when 0, take the plain
+                                     update v^{p+1} = G(v^p) of Algorithm 1 */
+    double helmholtz_tol;         /* target error reduction of the CN Helmholtz solve (Chebyshev) */
+} pic_config;
+
+/* Initial particles of one species. */
+typedef struct {
+    int64_t np;       /* number of macro-particles */
+    double q, m;      /* charge and mass per macro-particle */
+    const double* x;  /* 3 * np positions (SoA, physical units) */
+    const double* v;  /* 3 * np velocities (SoA) */
+    int32_t on_device;
+} pic_particles;
+
+/* Optional device allocator (for example the caller's caching allocator).  When it is
+ * absent the library uses cudaMalloc / cudaFree.  `stream` is the context's stream. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} pic_allocator;
+
+typedef struct {
+    int32_t steps_done;   /* steps committed by this call */
+    int32_t iterations;   /* Picard iterations of the last step (p + 1 at convergence) */
+    int32_t converged;    /* 1 if the last step met picard_tol */
+    int32_t total_iterations; /* Picard iterations summed over the committed steps */
+    double e_v, e_J;      /* the last step's final velocity and current fixed-point errors */
+} pic_step_info;
+
+typedef struct {
+    double K;      /* sum_i m |v_i|^2 / 2 (Eq. (particle-energy)) */
+    double W;      /* sum_g (|E_g|^2 / (2 sigma1) + |B_g|^2 / (2 sigma2)) dV (Eq. (field-energy)) */
+    double total;  /* K + W (Eq. (total-discrete-energy)) */
+} pic_energy_t;
+
+/* Diagnostics of the last committed step (valid when the config has diagnostics = 1). */
+typedef struct {
+    double gauge_max, gauge_rms;   /* G_h = psi / kappa^2 + div_h A at n+1 (Eq. (gauge-diagnostic)) */
+    double gauss_max, gauss_rms;   /* R_h = div_h E - sigma1 rho at n+1 (Eq. (gauss-diagnostic)) */
+    double continuity_max;         /* max |rho^{n+1} - rho^n + dt div_h J^{n+1/2}| */
+    double RA_max, RA_rms;         /* chain-rule residual over particles (Eq. (RA-test)) */
+    double partition_max;          /* max_i |sum_g Sbar_ig - 1| (Appendix A) */
+    double particle_work;          /* sum_i q vbar_i . Ebar_i (Eq. (power-test), left) */
+    double mesh_work;              /* sum_g J . E^{n+1/2} dV (Eq. (power-test), right) */
+    double R_field, R_particle, R_total; /* Eq. (R-field), (R-particle), (R-total) */
+    double K0, W0, K1, W1;         /* energies before and after the step */
+    int32_t picard_iterations;
+    double e_v, e_J;
+} pic_diag_t;
+
+/* A full state, for checkpoint/restart and for inspection.  Caller-owned buffers:
+ * x, v, P, vprev: 3 * np each; phi, psi, rho: ncell each; A, U: 3 * ncell each.
+ * Particles are in the order they were given to pic_init. */
+typedef struct {
+    double *x, *v, *P, *vprev;
+    double *phi, *psi, *rho;
+    double *A, *U;
+    int32_t on_device;
+} pic_state_view;
+
+/* Outputs of one Picard-iteration body (pic_iterate).  Caller-owned buffers with the
+ * same sizes as in pic_state_view; J has 3 * ncell entries. */
+typedef struct {
+    double *J, *rho, *phi, *psi, *A, *U;  /* mesh: J^{n+1/2,p} and the level-(n+1,p) fields */
+    double *x, *P, *v;                    /* particles: x^{n+1,p}, P^{n+1,p}, v^{n+1,p+1} */
+    int32_t on_device;
+} pic_iterate_out;
+
+/* Live per-phase timing of the library's own kernels (CUDA events on the context stream)
+ * and a count of every kernel it launched, accumulated since the last reset. */
+typedef struct {
+    int64_t launches;            /* kernels launched */
+    int64_t push_launches;       /* fused push + next-orbit scatter launches (Picard iterations) */
+    double push_ms;              /* their summed event durations */
+    int64_t commit_launches;     /* final-sweep push launches */
+    double commit_ms;
+    int64_t scatter_launches;    /* first orbit-current scatter of each step */
+    double scatter_ms;
+    double mesh_ms;              /* continuity, CN Helmholtz solve, back-substitution, gather table */
+    double sort_ms;              /* counting sort by cell */
+    int64_t particle_pushes;     /* sum over push launches of the particle count */
+    int64_t push_pieces;         /* knot-free orbit pieces integrated by those pushes */
+    int64_t scatter_pieces;      /* orbit pieces integrated by their next-orbit scatters */
+} pic_profile_t;
+
+/* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
+ * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
+ * diagnostics off, local solves on, Chebyshev reduction 1e-17. */
+pic_status pic_config_default(pic_config* cfg);
+
+/* Create a context: copies the particles to the device, sorts them by cell, deposits
+ * rho^0 = sum_i q S_g(x_i)/dV + n0 with the null modes of Delta_h removed, solves
+ * -Delta_h phi^0 = sigma1 rho^0, sets psi = A = U = 0, P = m v and v^{n-1} = v (§5.4).
+ * `alloc` may be NULL.  `stream` is a cudaStream_t (NULL: the legacy default stream). */
+pic_status pic_init(const pic_config* cfg, const pic_particles* particles,
+                    const pic_allocator* alloc, void* stream, pic_ctx** out);
+
+/* Advance nsteps time steps (Algorithm 1 plus the final consistency sweep of §5.4).
+ * `info` may be NULL.  Returns PIC_ERR_NO_CONVERGENCE (state kept at the last committed
+ * step) when a step reaches picard_max unless accept_unconverged is set. */
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps, pic_step_info* info);
+
+/* Kinetic, field and total energy of the current state (§4.1), FP64 sums. */
+pic_status pic_energy(pic_ctx* ctx, pic_energy_t* out);
+
+/* Diagnostics of the last committed step (§5.1-§5.3).  PIC_ERR_ARG if none is available. */
+pic_status pic_diagnostics(pic_ctx* ctx, pic_diag_t* out);
+
+/* Copy the full state out (checkpoint) / in (restart).  pic_set_state also accepts a
+ * state that was not produced by the library; it does not re-solve any field. */
+pic_status pic_get_state(pic_ctx* ctx, const pic_state_view* dst);
+pic_status pic_set_state(pic_ctx* ctx, const pic_state_view* src);
+
+/* Run one body of the Algorithm 1 loop from the given end-of-step velocity iterate
+ * v^{n+1,p} (3 * np, particles in pic_init order) without committing anything, and copy
+ * out the orbit current, the new mesh fields and the pushed particles. */
+pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, const pic_iterate_out* out);
+
+/* Switch live profiling on (1) or off (0).  If `out` is non-NULL the accumulated profile is
+ * copied there (after synchronising the stream) and the accumulators are reset. */
+pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
+
+/* One-line description of the last error on this context ("" if none). */
+const char* pic_last_error(const pic_ctx* ctx);
+
+/* Free every device buffer of the context (on its stream) and the context itself. */
+void pic_destroy(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -17,6 +17,18 @@ Readings of points the paper leaves open (each is listed in the design notes):
   are the accepted step and feed the diagnostics.
 * Not converged after p = 0..p_max: the step is reported as not converged (the
   caller keeps the old state).
+* Accelerated fixed point (§4.8 states that conservation holds for any converged
+  solver, accelerated fixed-point methods included).  A particle whose orbit crosses a
+  knot on an axis where it moves very little (|beta_a| < 0.1 cells, "creeping") has a
+  step force that is very sensitive to its own velocity: the orbit average of d_j S in
+  D_i A changes with the fraction of the path beyond the knot.  The particle-local
+  feedback can exceed 1, and plain Picard then stalls or cycles on it.  With
+  ``picard_accel`` each iteration therefore solves, for the creeping particles only, the
+  particle's own equation v = G_i(v) with the iteration's fields held fixed (secant steps
+  per component, at most LOCAL_STEPS evaluations, keeping the best iterate); every other
+  particle takes Algorithm 1's update v^{p+1} = G(v^p).  The outer loop then contracts at
+  the rate of the weak particle-field coupling.  With ``picard_accel=False`` every particle
+  takes the plain update.
 * Initial charge: rho_g = sum_i q_i S_g(x_i) / dV plus the ion background, with the
   null modes of Delta_h (the mean and the checkerboards) removed; Poisson's 1/eps0 is
   read as sigma1.
@@ -31,6 +43,10 @@ import numpy as np
 from . import mesh, orbit
 
 CHUNK = 32768
+BETA_CREEP = 0.1      # cells: "creeping" knot crossings get a particle-local solve
+LOCAL_STEPS = 8       # at most this many extra push evaluations per creeping particle
+LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
+OMEGA_MAX = 8.0       # bound on the secant step factor
 
 
 @dataclass
@@ -44,6 +60,7 @@ class Config:
     picard_tol: float = 1e-14
     picard_max: int = 16
     split: bool = True
+    picard_accel: bool = True    # per-particle secant relaxation of the Picard update (see step())
     quadrature: str = "closed"   # "closed" (Appendices A/B) or "gauss" (§4.7 split Gauss rule)
     nq: int = 16
     n0: float = 1.0              # ion background density (§5.4)
@@ -138,35 +155,102 @@ def picard_iteration(st, v_it, cfg, grid, diagnostics=False):
     # midpoint mesh fields
     gphi_half = mesh.grad(0.5 * (phi1 + st.phi), grid)
     U_half = 0.5 * (U1 + st.U)
-    npart = st.xi.shape[0]
-    P1 = np.empty((npart, 3))
-    xi1 = np.empty((npart, 3))
-    v_new = np.empty((npart, 3))
-    diag = {"RA": np.empty((npart, 3)), "pu": np.empty(npart), "pwork": 0.0} if diagnostics else None
-    for sl in _chunks(npart):
-        ow = orbit_weights(st.xi[sl], beta[sl], cfg, grid)
-        gphibar = orbit.gather(gphi_half, ow).T                     # (np, 3)  Eq. (gphibar-definition)
-        DA = orbit.orbit_gradient(st.A, A1, ow)                     # (np, l, j)  Eq. (DA-def)
-        DAT_vbar = np.einsum("ilj,il->ij", DA, vbar[sl])            # ((D A)^T vbar)_j
-        P1[sl] = st.P[sl] + dt * (-st.q * gphibar + st.q * DAT_vbar)   # Eq. (orbit-P-update)
-        xend = st.xi[sl] + beta[sl]                                  # Eq. (orbit-x-update), unwrapped
-        xi1[sl] = wrap_cells(xend, grid.n)
-        A_end = orbit.point_gather(A1, xi1[sl], grid).T              # A_h^{n+1}(x^{n+1})
-        v_new[sl] = (P1[sl] - st.q * A_end) / st.m                   # Eq. (orbit-v-update)
-        if diagnostics:
-            Ubar = orbit.gather(U_half, ow).T                        # Eq. (Ubar-def)
-            A_start = orbit.point_gather(st.A, st.xi[sl], grid).T
-            DA_vbar = np.einsum("ilj,ij->il", DA, vbar[sl])          # (D A) vbar
-            diag["RA"][sl] = A_end - A_start - dt * (Ubar + DA_vbar)     # Eq. (RA-test)
-            diag["pu"][sl] = np.sum(ow.w, axis=1) - 1.0                  # Appendix A partition of unity
-            Ebar = -gphibar - Ubar                                       # Eq. (orbit-E-gather)
-            diag["pwork"] += float(np.sum(st.q * vbar[sl] * Ebar))
-    out = dict(J=J, rho=rho1, phi=phi1, psi=psi1, A=A1, U=U1, P=P1, xi=xi1, v_new=v_new, vbar=vbar)
+    pushed = push_particles(st.xi, st.v, st.P, v_it, st.q, st.m, st.A, A1, gphi_half, U_half, cfg, grid,
+                            diagnostics)
+    P1, xi1, v_new = pushed["P"], pushed["xi"], pushed["v_new"]
+    diag = pushed.get("diag")
+    out = dict(J=J, rho=rho1, phi=phi1, psi=psi1, A=A1, U=U1, P=P1, xi=xi1, v_new=v_new, vbar=vbar,
+               gphi_half=gphi_half, U_half=U_half)
     if diagnostics:
         E_half = -gphi_half - U_half
         diag["mwork"] = float(np.sum(J * E_half) * grid.dV)               # sum_g J . E dV
         out["diag"] = diag
     return out
+
+
+def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, diagnostics=False):
+    """Orbit gather and canonical-momentum push of Algorithm 1 for the given particles.
+
+    Uses the midpoint mesh fields of the current iterate: grad_h phi^{n+1/2} (3, n...),
+    A^n and A^{n+1} for the orbit-discrete gradient, and U^{n+1/2} (diagnostics only).
+    """
+    H = np.asarray(grid.H)
+    dt = cfg.dt
+    vbar = 0.5 * (v_it + v)
+    beta = dt * vbar / H
+    npart = xi.shape[0]
+    P1 = np.empty((npart, 3))
+    xi1 = np.empty((npart, 3))
+    v_new = np.empty((npart, 3))
+    diag = {"RA": np.empty((npart, 3)), "pu": np.empty(npart), "pwork": 0.0} if diagnostics else None
+    for sl in _chunks(npart):
+        ow = orbit_weights(xi[sl], beta[sl], cfg, grid)
+        gphibar = orbit.gather(gphi_half, ow).T                     # (np, 3)  Eq. (gphibar-definition)
+        DA = orbit.orbit_gradient(A0, A1, ow)                       # (np, l, j)  Eq. (DA-def)
+        DAT_vbar = np.einsum("ilj,il->ij", DA, vbar[sl])            # ((D A)^T vbar)_j
+        P1[sl] = P[sl] + dt * (-q * gphibar + q * DAT_vbar)          # Eq. (orbit-P-update)
+        xend = xi[sl] + beta[sl]                                     # Eq. (orbit-x-update), unwrapped
+        xi1[sl] = wrap_cells(xend, grid.n)
+        A_end = orbit.point_gather(A1, xi1[sl], grid).T              # A_h^{n+1}(x^{n+1})
+        v_new[sl] = (P1[sl] - q * A_end) / m                         # Eq. (orbit-v-update)
+        if diagnostics:
+            Ubar = orbit.gather(U_half, ow).T                        # Eq. (Ubar-def)
+            A_start = orbit.point_gather(A0, xi[sl], grid).T
+            DA_vbar = np.einsum("ilj,ij->il", DA, vbar[sl])          # (D A) vbar
+            diag["RA"][sl] = A_end - A_start - dt * (Ubar + DA_vbar)     # Eq. (RA-test)
+            diag["pu"][sl] = np.sum(ow.w, axis=1) - 1.0                  # Appendix A partition of unity
+            Ebar = -gphibar - Ubar                                       # Eq. (orbit-E-gather)
+            diag["pwork"] += float(np.sum(q * vbar[sl] * Ebar))
+    out = {"P": P1, "xi": xi1, "v_new": v_new}
+    if diagnostics:
+        out["diag"] = diag
+    return out
+
+
+def creeping(xi, beta):
+    """Particles whose orbit crosses a knot on an axis with 0 < |beta_a| < BETA_CREEP (cells)."""
+    f = np.zeros(xi.shape[0], dtype=bool)
+    for a in range(3):
+        b = beta[:, a]
+        f |= (np.floor(xi[:, a] + b) != np.floor(xi[:, a])) & (np.abs(b) < BETA_CREEP) & (b != 0)
+    return f
+
+
+def local_solve(st, v_it, it, cfg, grid):
+    """Next iterate: G(v^p) for most particles; for the creeping ones the root of
+    v = G_i(v) with this iteration's fields fixed (secant per component, best iterate kept)."""
+    H = np.asarray(grid.H)
+    G = it["v_new"]
+    v_next = G.copy()
+    beta = cfg.dt * 0.5 * (v_it + st.v) / H
+    idx = np.nonzero(creeping(st.xi, beta))[0]
+    if idx.size == 0:
+        return v_next
+
+    def Gf(u):
+        return push_particles(st.xi[idx], st.v[idx], st.P[idx], u, st.q, st.m, st.A, it["A"], it["gphi_half"],
+                              it["U_half"], cfg, grid)["v_new"]
+
+    u0, r0 = v_it[idx], G[idx] - v_it[idx]
+    u1 = G[idx]
+    r1 = Gf(u1) - u1
+    scale = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)[:, None]
+    best_u = np.where(np.abs(r1) < np.abs(r0), u1, u0)
+    best_r = np.minimum(np.abs(r1), np.abs(r0))
+    for _ in range(LOCAL_STEPS - 1):
+        if np.all(best_r <= scale):
+            break
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sec = -(u1 - u0) / (r1 - r0)
+        sec = np.where(np.isfinite(sec), np.clip(sec, -OMEGA_MAX, OMEGA_MAX), 1.0)
+        u2 = u1 + sec * r1
+        r2 = Gf(u2) - u2
+        better = np.abs(r2) < best_r
+        best_u = np.where(better, u2, best_u)
+        best_r = np.where(better, np.abs(r2), best_r)
+        u0, r0, u1, r1 = u1, r1, u2, r2
+    v_next[idx] = best_u
+    return v_next
 
 
 def j_scale(st, grid):
@@ -187,18 +271,24 @@ def step(st, cfg):
     converged = False
     for p in range(cfg.picard_max + 1):
         it = picard_iteration(st, v_it, cfg, grid)
-        e_v = np.linalg.norm(it["v_new"] - v_it) / np.linalg.norm(it["v_new"])
-        e_J = np.inf if J_prev is None else np.linalg.norm(it["J"] - J_prev) / (np.linalg.norm(it["J"]) + jsc)
+        vnorm = np.linalg.norm(it["v_new"])
+        e_v = np.linalg.norm(it["v_new"] - v_it) / vnorm if vnorm > 0 else 0.0   # no particles: no error
+        if J_prev is None:
+            e_J = np.inf
+        else:
+            num, den = np.linalg.norm(it["J"] - J_prev), np.linalg.norm(it["J"]) + jsc
+            e_J = num / den if den > 0 else (np.inf if num > 0 else 0.0)   # no current at all: no error
         hist.append((float(e_v), float(e_J)))
         if e_v <= cfg.picard_tol and e_J <= cfg.picard_tol:
             converged = True
             break
-        v_it = it["v_new"]
+        v_it = local_solve(st, v_it, it, cfg, grid) if cfg.picard_accel else it["v_new"]
         J_prev = it["J"]
     info = {"converged": converged, "iterations": len(hist), "errors": hist}
     if not converged:
         return st, info
-    fin = picard_iteration(st, it["v_new"], cfg, grid, diagnostics=True)
+    v_fin = local_solve(st, v_it, it, cfg, grid) if cfg.picard_accel else it["v_new"]
+    fin = picard_iteration(st, v_fin, cfg, grid, diagnostics=True)
     new = State(xi=fin["xi"], v=fin["v_new"], P=fin["P"], vprev=st.v.copy(), q=st.q, m=st.m,
                 phi=fin["phi"], psi=fin["psi"], A=fin["A"], U=fin["U"], rho=fin["rho"])
     K0, W0 = energy(st, cfg)

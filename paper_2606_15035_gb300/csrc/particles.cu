@@ -1,0 +1,770 @@
+// Particle kernels of the orbit-averaged PIC step (FP64, sm_103a).
+//
+// One particle per thread, grid-stride loops, particles in structure-of-arrays layout
+// (component c of particle i at c * np + i) and cell-sorted so that neighbouring
+// threads gather the same mesh nodes.  Mesh data for the gather come from a per-node
+// table of 12 doubles: A^n (3), A^{n+1,p} (3), grad_h phi^{n+1/2,p} (3), U^{n+1/2,p} (3).
+#include <cmath>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+__constant__ double c_gauss_t[16];
+__constant__ double c_gauss_w[16];
+
+// Gauss-Legendre nodes on [0, 1] by Newton's method on the Legendre polynomial P_nq
+// (three-term recurrence), weights 1 / ((1 - x^2) P'(x)^2) mapped from [-1, 1].
+void set_gauss_rule(int nq) {
+    double t[16] = {0}, w[16] = {0};
+    for (int k = 0; k < nq; ++k) {
+        double x = std::cos(M_PI * (k + 0.75) / (nq + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int j = 2; j <= nq; ++j) {
+                double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            double pn = nq == 0 ? 1.0 : (nq == 1 ? x : p1);
+            double pm = nq == 1 ? 1.0 : p0;
+            dp = nq * (x * pn - pm) / (x * x - 1.0);
+            double dx = pn / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-17) break;
+        }
+        t[k] = 0.5 * (1.0 - x);
+        w[k] = 1.0 / ((1.0 - x * x) * dp * dp);  // = 0.5 * 2 / ((1 - x^2) P'^2)
+    }
+    cudaMemcpyToSymbol(c_gauss_t, t, sizeof(t));
+    cudaMemcpyToSymbol(c_gauss_w, w, sizeof(w));
+}
+
+namespace {
+
+
+// ---- orbit current scatter (Eq. (orbit-current)) -------------------------------------
+
+// J_c[g] += w_c * Sbar contribution of every piece (closed form, Appendix A).
+__device__ __forceinline__ int scatter_closed(const StepParams& p, const double x0[3], const double beta[3],
+                                              const double w[3], double* __restrict__ J) {
+    const int64_t N = p.m.ncell;
+    return for_each_segment(x0, beta, true, [&](const Segment<double>& sg) {
+        double I[8];
+        int64_t g[8];
+        segment_weights8(sg, beta, I);
+        segment_nodes8(sg, p.m, g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            atomicAdd(J + g[k], w[0] * I[k]);
+            atomicAdd(J + N + g[k], w[1] * I[k]);
+            atomicAdd(J + 2 * N + g[k], w[2] * I[k]);
+        }
+    });
+}
+
+// Same with an n_q-point Gauss rule on each piece (split) or on the whole path (unsplit).
+__device__ __forceinline__ int scatter_gauss(const StepParams& p, const double x0[3], const double beta[3],
+                                             const double w[3], double* __restrict__ J) {
+    const int64_t N = p.m.ncell;
+    return for_each_segment(x0, beta, p.split != 0, [&](const Segment<double>& sg) {
+        for (int qd = 0; qd < p.nq; ++qd) {
+            double s = sg.s0 + sg.h * c_gauss_t[qd];
+            double wq = sg.h * c_gauss_w[qd];
+            double xq[3] = {x0[0] + s * beta[0], x0[1] + s * beta[1], x0[2] + s * beta[2]};
+            int64_t g[8];
+            double S[8];
+            point_weights8(xq, p.m, g, S);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                double f = wq * S[k];
+                atomicAdd(J + g[k], w[0] * f);
+                atomicAdd(J + N + g[k], w[1] * f);
+                atomicAdd(J + 2 * N + g[k], w[2] * f);
+            }
+        }
+    });
+}
+
+template <int QUAD>
+__device__ __forceinline__ int scatter_orbit(const StepParams& p, const double x0[3], const double beta[3],
+                                             const double w[3], double* J) {
+    if constexpr (QUAD == 0) return scatter_closed(p, x0, beta, w, J);
+    else return scatter_gauss(p, x0, beta, w, J);
+}
+
+// ---- push (Eq. (orbit-push)) -------------------------------------------------------
+
+struct PushAcc {
+    double gphi[3];   // orbit gather of grad_h phi^{n+1/2} (Eq. (gphibar-definition))
+    double F[3];      // (D_i A)^T vbar (Eq. (DA-def), Appendix B)
+    double Ubar[3];   // orbit gather of U^{n+1/2} (Eq. (Ubar-def)), diagnostics only
+    double DAv[3];    // (D_i A) vbar, diagnostics only
+    double pu;        // sum_g Sbar_ig, diagnostics only
+};
+
+template <bool DIAG>
+__device__ __forceinline__ void push_piece_closed(const StepParams& p, const Segment<double>& sg, const double beta[3],
+                                                  const double vb[3], const double* __restrict__ table, PushAcc& acc) {
+    double I[8];
+    int64_t g[8];
+    segment_weights8(sg, beta, I);
+    segment_nodes8(sg, p.m, g);
+    const double s = sg.s0, h = sg.h;
+    double am[8], cc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double* t = table + 12 * g[k];
+        double an = t[0] * vb[0] + t[1] * vb[1] + t[2] * vb[2];   // A^n_g . vbar
+        double a1 = t[3] * vb[0] + t[4] * vb[1] + t[5] * vb[2];   // A^{n+1}_g . vbar
+        am[k] = (1.0 - s) * an + s * a1;                          // A^{(m)}_nu . vbar
+        cc[k] = a1 - an;                                          // C^{(m)}_nu . vbar
+        acc.gphi[0] += I[k] * t[6];
+        acc.gphi[1] += I[k] * t[7];
+        acc.gphi[2] += I[k] * t[8];
+        if constexpr (DIAG) {
+            acc.Ubar[0] += I[k] * t[9];
+            acc.Ubar[1] += I[k] * t[10];
+            acc.Ubar[2] += I[k] * t[11];
+            acc.pu += I[k];
+        }
+    }
+    AxisPoly<double> px = axis_poly(sg.r[0], beta[0]);
+    AxisPoly<double> py = axis_poly(sg.r[1], beta[1]);
+    AxisPoly<double> pz = axis_poly(sg.r[2], beta[2]);
+    // transverse integrals T0, T1 per derivative direction j and transverse offsets
+    double t0x[4], t1x[4], t0y[4], t1y[4], t0z[4], t1z[4];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            transverse_integrals(quad_product(py.L[a], py.M[a], pz.L[b], pz.M[b]), h, t0x[a + 2 * b], t1x[a + 2 * b]);
+            transverse_integrals(quad_product(px.L[a], px.M[a], pz.L[b], pz.M[b]), h, t0y[a + 2 * b], t1y[a + 2 * b]);
+            transverse_integrals(quad_product(px.L[a], px.M[a], py.L[b], py.M[b]), h, t0z[a + 2 * b], t1z[a + 2 * b]);
+        }
+    // [(D A)^T vbar]_j = sum_nu (sigma_{nu_j} / H_j) (A^{(m)}_nu.vbar T0 + C_nu.vbar T1)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            int k;
+            k = 2 * a + 4 * b;  // nu = (0, a, b) vs (1, a, b)
+            acc.F[0] += p.invH[0] * (t0x[a + 2 * b] * (am[k + 1] - am[k]) + t1x[a + 2 * b] * (cc[k + 1] - cc[k]));
+            k = a + 4 * b;      // nu = (a, 0, b) vs (a, 1, b)
+            acc.F[1] += p.invH[1] * (t0y[a + 2 * b] * (am[k + 2] - am[k]) + t1y[a + 2 * b] * (cc[k + 2] - cc[k]));
+            k = a + 2 * b;      // nu = (a, b, 0) vs (a, b, 1)
+            acc.F[2] += p.invH[2] * (t0z[a + 2 * b] * (am[k + 4] - am[k]) + t1z[a + 2 * b] * (cc[k + 4] - cc[k]));
+        }
+    if constexpr (DIAG) {
+        // [(D A) vbar]_l = sum_nu (A^{(m)}_{l nu} G0_nu + C_{l nu} G1_nu),
+        // G_nu = sum_j sigma_{nu_j} vbar_j / H_j * T_j(transverse of nu)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int nx = k & 1, ny = (k >> 1) & 1, nz = (k >> 2) & 1;
+            const double sx = nx ? 1.0 : -1.0, sy = ny ? 1.0 : -1.0, sz = nz ? 1.0 : -1.0;
+            double G0 = sx * p.invH[0] * vb[0] * t0x[ny + 2 * nz] + sy * p.invH[1] * vb[1] * t0y[nx + 2 * nz] +
+                        sz * p.invH[2] * vb[2] * t0z[nx + 2 * ny];
+            double G1 = sx * p.invH[0] * vb[0] * t1x[ny + 2 * nz] + sy * p.invH[1] * vb[1] * t1y[nx + 2 * nz] +
+                        sz * p.invH[2] * vb[2] * t1z[nx + 2 * ny];
+            const double* t = table + 12 * g[k];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                double Am = (1.0 - s) * t[l] + s * t[3 + l];
+                acc.DAv[l] += Am * G0 + (t[3 + l] - t[l]) * G1;
+            }
+        }
+    }
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void push_piece_gauss(const StepParams& p, const Segment<double>& sg, const double x0[3],
+                                                 const double beta[3], const double vb[3],
+                                                 const double* __restrict__ table, PushAcc& acc) {
+    for (int qd = 0; qd < p.nq; ++qd) {
+        const double s = sg.s0 + sg.h * c_gauss_t[qd];
+        const double wq = sg.h * c_gauss_w[qd];
+        double xq[3] = {x0[0] + s * beta[0], x0[1] + s * beta[1], x0[2] + s * beta[2]};
+        int c[3];
+        double r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double f = floor(xq[a]);
+            c[a] = (int)f;
+            r[a] = xq[a] - f;
+        }
+        Segment<double> cs;
+        cs.cell[0] = c[0];
+        cs.cell[1] = c[1];
+        cs.cell[2] = c[2];
+        int64_t g[8];
+        segment_nodes8(cs, p.m, g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int nx = k & 1, ny = (k >> 1) & 1, nz = (k >> 2) & 1;
+            const double wx = nx ? r[0] : 1.0 - r[0], wy = ny ? r[1] : 1.0 - r[1], wz = nz ? r[2] : 1.0 - r[2];
+            const double W = wq * wx * wy * wz;
+            const double dW[3] = {wq * (nx ? p.invH[0] : -p.invH[0]) * wy * wz,
+                                  wq * (ny ? p.invH[1] : -p.invH[1]) * wx * wz,
+                                  wq * (nz ? p.invH[2] : -p.invH[2]) * wx * wy};
+            const double* t = table + 12 * g[k];
+            const double an = t[0] * vb[0] + t[1] * vb[1] + t[2] * vb[2];
+            const double a1 = t[3] * vb[0] + t[4] * vb[1] + t[5] * vb[2];
+            const double as = (1.0 - s) * an + s * a1;           // A_g(s) . vbar
+            acc.gphi[0] += W * t[6];
+            acc.gphi[1] += W * t[7];
+            acc.gphi[2] += W * t[8];
+            acc.F[0] += as * dW[0];
+            acc.F[1] += as * dW[1];
+            acc.F[2] += as * dW[2];
+            if constexpr (DIAG) {
+                acc.Ubar[0] += W * t[9];
+                acc.Ubar[1] += W * t[10];
+                acc.Ubar[2] += W * t[11];
+                acc.pu += W;
+                const double vdW = vb[0] * dW[0] + vb[1] * dW[1] + vb[2] * dW[2];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) acc.DAv[l] += ((1.0 - s) * t[l] + s * t[3 + l]) * vdW;
+            }
+        }
+    }
+}
+
+// Point interpolant of columns [col, col+3) of the table at a wrapped position.
+__device__ __forceinline__ void point_gather3(const StepParams& p, const double xq[3], const double* __restrict__ table,
+                                              int col, double out[3]) {
+    int64_t g[8];
+    double w[8];
+    point_weights8(xq, p.m, g, w);
+    out[0] = out[1] = out[2] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double* t = table + 12 * g[k] + col;
+        out[0] += w[k] * t[0];
+        out[1] += w[k] * t[1];
+        out[2] += w[k] * t[2];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_partial(double* partials, int slot, double v, double* sm, bool is_max) {
+    double r = is_max ? block_max(v, sm) : block_sum(v, sm);
+    if (threadIdx.x == 0) partials[slot * MAX_BLOCKS + blockIdx.x] = r;
+}
+
+// ---- kernels ----------------------------------------------------------------------
+
+__global__ void k_init_positions(StepParams p, const double* __restrict__ x, double* __restrict__ xi,
+                                 int64_t* __restrict__ id) {
+    const int64_t np = p.np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xi[a * np + i] = wrap_pos(x[a * np + i] * p.invH[a], (double)p.m.n[a]);
+        id[i] = i;
+    }
+}
+
+__global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, double* __restrict__ rho) {
+    const int64_t np = p.np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        double x[3] = {xi[i], xi[np + i], xi[2 * np + i]};
+        int64_t g[8];
+        double w[8];
+        point_weights8(x, p.m, g, w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(rho + g[k], p.q_dV * w[k]);
+    }
+}
+
+// v^{n+1,0} = 2 v^n - v^{n-1} (Algorithm 1, extrapolated start) unless an iterate is given;
+// then the orbit current of that iterate, and sum_i |v^n_i| for the e_J floor.
+template <int QUAD>
+__global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, const double* __restrict__ v,
+                                const double* __restrict__ vprev, const double* __restrict__ vgiven,
+                                double* __restrict__ vit, double* __restrict__ J, double* __restrict__ partials,
+                                int* __restrict__ status) {
+    __shared__ double sm[32];
+    const int64_t np = p.np;
+    double jsc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        double x0[3], vn[3], vi[3], beta[3], w[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x0[a] = xi[a * np + i];
+            vn[a] = v[a * np + i];
+            vi[a] = vgiven ? vgiven[a * np + i] : 2.0 * vn[a] - vprev[a * np + i];
+            vit[a * np + i] = vi[a];
+            double vb = 0.5 * (vi[a] + vn[a]);
+            beta[a] = p.dt * vb * p.invH[a];
+            w[a] = p.q_dV * vb;
+        }
+        jsc += sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+        if (scatter_orbit<QUAD>(p, x0, beta, w, J) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+    }
+    write_partial<double>(partials, S_JSCALE, jsc, sm, false);
+}
+
+// Constants of the particle-local solve for "creeping" particles (see k_local).
+constexpr double BETA_CREEP = 0.1;   // cells
+constexpr int LOCAL_STEPS = 8;       // push evaluations per creeping particle
+constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
+constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
+
+// Does the orbit cross a knot on an axis where it moves less than BETA_CREEP cells?
+__device__ __forceinline__ bool is_creeping(const double x0[3], const double beta[3]) {
+    bool f = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        f |= (beta[a] != 0.0) && (fabs(beta[a]) < BETA_CREEP) && (floor(x0[a] + beta[a]) != floor(x0[a]));
+    return f;
+}
+
+struct PushOut {
+    double Pw[3], xe[3], Ae[3], vw[3];
+    int nseg;
+};
+
+// G(u): the Algorithm 1 push of one particle for the end-of-step iterate u with the
+// current mesh table: orbit vbar = (u + v^n)/2, P^{n+1} (Eq. (orbit-P-update)),
+// x^{n+1} (Eq. (orbit-x-update)) and v^{n+1} = (P^{n+1} - q A_h^{n+1}(x^{n+1})) / m.
+template <int QUAD, bool DIAG>
+__device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3], const double vn[3],
+                                          const double Pn[3], const double u[3], const double* __restrict__ table,
+                                          PushAcc& acc, PushOut& o) {
+    double vb[3], beta[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vb[a] = 0.5 * (u[a] + vn[a]);
+        beta[a] = p.dt * vb[a] * p.invH[a];
+    }
+    acc = PushAcc{};
+    if constexpr (QUAD == 0) {
+        o.nseg = for_each_segment(x0, beta, true,
+                                  [&](const Segment<double>& sg) { push_piece_closed<DIAG>(p, sg, beta, vb, table, acc); });
+    } else {
+        o.nseg = for_each_segment(x0, beta, p.split != 0, [&](const Segment<double>& sg) {
+            push_piece_gauss<DIAG>(p, sg, x0, beta, vb, table, acc);
+        });
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.Pw[a] = Pn[a] + p.dt * (-p.q * acc.gphi[a] + p.q * acc.F[a]);
+        o.xe[a] = wrap_pos(x0[a] + beta[a], (double)p.m.n[a]);
+    }
+    point_gather3(p, o.xe, table, 3, o.Ae);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o.vw[a] = (o.Pw[a] - p.q * o.Ae[a]) / p.mass;
+}
+
+// The Algorithm 1 push for iterate vit, then either
+//   (iterate)  the next iterate and its orbit current into Jnext, plus the e_v partial sums.
+//              The next iterate is G(v^p); with p.accel, creeping particles are instead
+//              appended to a list and solved locally by k_local (which also scatters them);
+//   (commit)   x^{n+1}, P^{n+1}, v^{n+1} and (optionally) the particle diagnostics.
+template <int QUAD, bool COMMIT, bool DIAG>
+__global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __restrict__ xi,
+                                                  const double* __restrict__ v, const double* __restrict__ P,
+                                                  const double* __restrict__ vit, const double* __restrict__ table,
+                                                  double* __restrict__ vnew, double* __restrict__ Jnext,
+                                                  double* __restrict__ xi_out, double* __restrict__ P_out,
+                                                  int32_t* __restrict__ creep_list, int* __restrict__ creep_count,
+                                                  double* __restrict__ partials, int* __restrict__ status) {
+    __shared__ double sm[32];
+    const int64_t np = p.np;
+    double ev_num = 0.0, ev_den = 0.0, pieces_push = 0.0, pieces_scatter = 0.0;
+    double k1 = 0.0, pwork = 0.0, ra_sq = 0.0, ra_max = 0.0, pu_max = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        double x0[3], vn[3], vi[3], Pn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x0[a] = xi[a * np + i];
+            vn[a] = v[a * np + i];
+            vi[a] = vit[a * np + i];
+            Pn[a] = P[a * np + i];
+        }
+        PushAcc acc;
+        PushOut o;
+        push_eval<QUAD, DIAG>(p, x0, vn, Pn, vi, table, acc, o);
+        if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        pieces_push += (double)o.nseg;
+        if (!(isfinite(o.vw[0]) && isfinite(o.vw[1]) && isfinite(o.vw[2]))) atomicOr(status, DEV_ERR_NONFINITE);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
+        if constexpr (!COMMIT) {
+            double beta_it[3], wv[3], bet2[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double d = o.vw[a] - vi[a];   // Picard residual r = G(v) - v
+                ev_num += d * d;
+                ev_den += o.vw[a] * o.vw[a];
+                beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
+                double vb2 = 0.5 * (o.vw[a] + vn[a]);
+                bet2[a] = p.dt * vb2 * p.invH[a];
+                wv[a] = p.q_dV * vb2;
+            }
+            if (p.accel && is_creeping(x0, beta_it)) {
+                int k = atomicAdd(creep_count, 1);
+                creep_list[k] = (int32_t)i;
+            } else {
+                int ns = scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext);
+                if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+                pieces_scatter += (double)ns;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xi_out[a * np + i] = o.xe[a];
+                P_out[a * np + i] = o.Pw[a];
+            }
+            if constexpr (DIAG) {
+                double As[3], vb[3];
+                point_gather3(p, x0, table, 0, As);                       // A_h^n(x^n)
+                double ra2 = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    vb[a] = 0.5 * (vi[a] + vn[a]);
+                    double ra = o.Ae[a] - As[a] - p.dt * (acc.Ubar[a] + acc.DAv[a]);   // Eq. (RA-test)
+                    ra2 += ra * ra;
+                    ra_max = fmax(ra_max, fabs(ra));
+                    pwork += p.q * vb[a] * (-acc.gphi[a] - acc.Ubar[a]);                // q vbar . Ebar
+                    k1 += 0.5 * p.mass * o.vw[a] * o.vw[a];
+                }
+                ra_sq += ra2;
+                pu_max = fmax(pu_max, fabs(acc.pu - 1.0));
+            }
+        }
+    }
+    if constexpr (!COMMIT) {
+        write_partial<double>(partials, S_EV_NUM, ev_num, sm, false);
+        write_partial<double>(partials, S_EV_DEN, ev_den, sm, false);
+        write_partial<double>(partials, S_PIECES_PUSH, pieces_push, sm, false);
+        write_partial<double>(partials, S_PIECES_SCATTER, pieces_scatter, sm, false);
+    } else if constexpr (DIAG) {
+        write_partial<double>(partials, S_K1, k1, sm, false);
+        write_partial<double>(partials, S_PWORK, pwork, sm, false);
+        write_partial<double>(partials, S_RA_SQ, ra_sq, sm, false);
+        write_partial<double>(partials, S_RA_MAX, ra_max, sm, true);
+        write_partial<double>(partials, S_PU_MAX, pu_max, sm, true);
+    }
+}
+
+// Particle-local solve of v = G_i(v) with the iteration's fields fixed, for the creeping
+// particles listed by k_push (§4.8 allows any converged solver).  Secant steps per
+// component from the pair (v^p, G(v^p)), (G(v^p), G(G(v^p))), ...: at most LOCAL_STEPS
+// push evaluations, stopping when every component's residual is below LOCAL_TOL times the
+// particle's speed; the best iterate per component is kept.  Then its orbit current.
+template <int QUAD>
+__global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* __restrict__ xi,
+                                                   const double* __restrict__ v, const double* __restrict__ P,
+                                                   const double* __restrict__ vit, const double* __restrict__ table,
+                                                   double* __restrict__ vnew, double* __restrict__ Jnext,
+                                                   const int32_t* __restrict__ creep_list,
+                                                   const int* __restrict__ creep_count, int* __restrict__ status) {
+    const int64_t np = p.np;
+    const int count = *creep_count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int64_t i = creep_list[k];
+        double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
+        double nrm = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x0[a] = xi[a * np + i];
+            vn[a] = v[a * np + i];
+            Pn[a] = P[a * np + i];
+            u0[a] = vit[a * np + i];
+            u1[a] = vnew[a * np + i];          // G(v^p) from k_push
+            r0[a] = u1[a] - u0[a];
+            nrm += u0[a] * u0[a];
+        }
+        const double tol = LOCAL_TOL * fmax(sqrt(nrm), 1e-300);
+        PushAcc acc;
+        PushOut o;
+        push_eval<QUAD, false>(p, x0, vn, Pn, u1, table, acc, o);
+        if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r1[a] = o.vw[a] - u1[a];
+            bool b1 = fabs(r1[a]) < fabs(r0[a]);
+            bu[a] = b1 ? u1[a] : u0[a];
+            br[a] = b1 ? fabs(r1[a]) : fabs(r0[a]);
+        }
+        for (int step = 0; step < LOCAL_STEPS - 1; ++step) {
+            if (br[0] <= tol && br[1] <= tol && br[2] <= tol) break;
+            double u2[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double sec = -(u1[a] - u0[a]) / (r1[a] - r0[a]);
+                sec = isfinite(sec) ? fmin(fmax(sec, -OMEGA_MAX), OMEGA_MAX) : 1.0;
+                u2[a] = u1[a] + sec * r1[a];
+            }
+            push_eval<QUAD, false>(p, x0, vn, Pn, u2, table, acc, o);
+            if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double r2 = o.vw[a] - u2[a];
+                if (fabs(r2) < br[a]) {
+                    br[a] = fabs(r2);
+                    bu[a] = u2[a];
+                }
+                u0[a] = u1[a];
+                r0[a] = r1[a];
+                u1[a] = u2[a];
+                r1[a] = r2;
+            }
+        }
+        double wv[3], bet2[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(bu[a])) atomicOr(status, DEV_ERR_NONFINITE);
+            vnew[a * np + i] = bu[a];
+            double vb2 = 0.5 * (bu[a] + vn[a]);
+            bet2[a] = p.dt * vb2 * p.invH[a];
+            wv[a] = p.q_dV * vb2;
+        }
+        if (scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+    }
+}
+
+__global__ void k_kinetic(StepParams p, const double* __restrict__ v, double* __restrict__ partials) {
+    __shared__ double sm[32];
+    const int64_t np = p.np;
+    double k = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = v[i], b = v[np + i], c = v[2 * np + i];
+        k += 0.5 * p.mass * (a * a + b * b + c * c);
+    }
+    write_partial<double>(partials, S_K, k, sm, false);
+}
+
+// ---- counting sort by cell of x^n -------------------------------------------------------
+
+__global__ void k_sort_keys(StepParams p, const double* __restrict__ xi, int32_t* __restrict__ key,
+                            int32_t* __restrict__ count) {
+    const int64_t np = p.np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int c0 = min(max((int)floor(xi[i]), 0), p.m.n[0] - 1);
+        int c1 = min(max((int)floor(xi[np + i]), 0), p.m.n[1] - 1);
+        int c2 = min(max((int)floor(xi[2 * np + i]), 0), p.m.n[2] - 1);
+        int32_t k = (int32_t)node_index(c0, c1, c2, p.m);
+        key[i] = k;
+        atomicAdd(count + k, 1);
+    }
+}
+
+// Exclusive scan of n ints in blocks of 1024 (phase 1: local scan and block totals).
+__global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t* __restrict__ totals,
+                             int64_t n) {
+    __shared__ int32_t s[1024];
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    int32_t v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int32_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) totals[blockIdx.x] = s[1023];
+}
+
+// Phase 2: one block scans the block totals sequentially in chunks of 1024.
+__global__ void k_scan_totals(int32_t* __restrict__ totals, int nb) {
+    __shared__ int32_t s[1024];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        int32_t v = i < nb ? totals[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int32_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) totals[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ totals, int64_t n) {
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    if (i < n) out[i] += totals[blockIdx.x];
+}
+
+// Place particle i at offset[key] + (arrival order within its cell) in the destination arrays.
+__global__ void k_sort_scatter(StepParams p, const int32_t* __restrict__ key, const int32_t* __restrict__ offset,
+                               int32_t* __restrict__ cursor, const double* __restrict__ xi, const double* __restrict__ v,
+                               const double* __restrict__ P, const double* __restrict__ vprev,
+                               const int64_t* __restrict__ id, double* __restrict__ xi_d, double* __restrict__ v_d,
+                               double* __restrict__ P_d, double* __restrict__ vprev_d, int64_t* __restrict__ id_d) {
+    const int64_t np = p.np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t k = key[i];
+        int64_t pos = (int64_t)offset[k] + atomicAdd(cursor + k, 1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xi_d[a * np + pos] = xi[a * np + i];
+            v_d[a * np + pos] = v[a * np + i];
+            P_d[a * np + pos] = P[a * np + i];
+            vprev_d[a * np + pos] = vprev[a * np + i];
+        }
+        id_d[pos] = id[i];
+    }
+}
+
+// dst[c, id[i]] = scale_c * src[c, i]  (device order -> caller order)
+__global__ void k_unpermute(int64_t np, const int64_t* __restrict__ id, const double* __restrict__ src,
+                            double* __restrict__ dst, double s0, double s1, double s2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = id[i];
+        dst[j] = s0 * src[i];
+        dst[np + j] = s1 * src[np + i];
+        dst[2 * np + j] = s2 * src[2 * np + i];
+    }
+}
+
+// dst[c, i] = scale_c * src[c, id[i]]  (caller order -> device order)
+__global__ void k_permute_in(int64_t np, const int64_t* __restrict__ id, const double* __restrict__ src,
+                             double* __restrict__ dst, double s0, double s1, double s2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = id[i];
+        dst[i] = s0 * src[j];
+        dst[np + i] = s1 * src[np + j];
+        dst[2 * np + i] = s2 * src[2 * np + j];
+    }
+}
+
+StepParams make_params(const Ctx& c) {
+    StepParams p;
+    p.m = c.m;
+    for (int a = 0; a < 3; ++a) {
+        p.H[a] = c.H[a];
+        p.invH[a] = c.invH[a];
+    }
+    p.dt = c.cfg.dt;
+    p.q = c.q;
+    p.mass = c.mass;
+    p.q_dV = c.q / c.dV;
+    p.np = c.np;
+    p.split = c.cfg.split_orbit_at_knots;
+    p.nq = c.cfg.nq;
+    p.accel = c.cfg.picard_accel;
+    return p;
+}
+
+}  // namespace
+
+int particle_blocks(const Ctx& c) {
+    int64_t b = (c.np + THREADS - 1) / THREADS;
+    int64_t cap = (int64_t)c.sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void launch_init_positions(Ctx& c, const double* x_dev) {
+    StepParams p = make_params(c);
+    k_init_positions<<<particle_blocks(c), THREADS, 0, c.stream>>>(p, x_dev, c.xi, c.id);
+    ++c.launches;
+}
+
+void launch_point_deposit(Ctx& c) {
+    StepParams p = make_params(c);
+    k_point_deposit<<<particle_blocks(c), THREADS, 0, c.stream>>>(p, c.xi, c.rho0);
+    ++c.launches;
+}
+
+void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null) {
+    StepParams p = make_params(c);
+    int nb = particle_blocks(c);
+    if (c.cfg.quadrature == PIC_QUAD_CLOSED)
+        k_first_scatter<0><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.vprev, v_iter_or_null, c.vit, J, c.partials,
+                                                         c.dev_status);
+    else
+        k_first_scatter<1><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.vprev, v_iter_or_null, c.vit, J, c.partials,
+                                                         c.dev_status);
+    ++c.launches;
+}
+
+void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag) {
+    StepParams p = make_params(c);
+    int nb = particle_blocks(c);
+    const bool closed = c.cfg.quadrature == PIC_QUAD_CLOSED;
+    if (!commit) cudaMemsetAsync(c.creep_count, 0, sizeof(int), c.stream);
+#define PIC_PUSH(Q, C, D)                                                                                        \
+    k_push<Q, C, D><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.xi_new, c.P_new, \
+                                                  c.creep_list, c.creep_count, c.partials, c.dev_status)
+    if (!commit) {
+        if (closed) PIC_PUSH(0, false, false);
+        else PIC_PUSH(1, false, false);
+    } else if (!diag) {
+        if (closed) PIC_PUSH(0, true, false);
+        else PIC_PUSH(1, true, false);
+    } else {
+        if (closed) PIC_PUSH(0, true, true);
+        else PIC_PUSH(1, true, true);
+    }
+#undef PIC_PUSH
+    ++c.launches;
+    if (!commit && c.cfg.picard_accel) {
+        int lb = std::max(1, std::min(nb, c.sms * 2));
+        if (closed)
+            k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.creep_list,
+                                                     c.creep_count, c.dev_status);
+        else
+            k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.creep_list,
+                                                     c.creep_count, c.dev_status);
+        ++c.launches;
+    }
+}
+
+void launch_kinetic(Ctx& c) {
+    StepParams p = make_params(c);
+    k_kinetic<<<particle_blocks(c), THREADS, 0, c.stream>>>(p, c.v, c.partials);
+    ++c.launches;
+}
+
+void launch_sort(Ctx& c) {
+    StepParams p = make_params(c);
+    const int64_t N = c.m.ncell;
+    int nb = particle_blocks(c);
+    cudaMemsetAsync(c.count, 0, sizeof(int32_t) * N, c.stream);
+    cudaMemsetAsync(c.cursor, 0, sizeof(int32_t) * N, c.stream);
+    k_sort_keys<<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.key, c.count);
+    ++c.launches;
+    int nsb = (int)((N + 1023) / 1024);
+    k_scan_local<<<nsb, 1024, 0, c.stream>>>(c.count, c.offset, c.scan_tmp, N);
+    ++c.launches;
+    k_scan_totals<<<1, 1024, 0, c.stream>>>(c.scan_tmp, nsb);
+    ++c.launches;
+    k_scan_add<<<nsb, 1024, 0, c.stream>>>(c.offset, c.scan_tmp, N);
+    ++c.launches;
+    // destinations: the free iterate/commit buffers of the step
+    k_sort_scatter<<<nb, THREADS, 0, c.stream>>>(p, c.key, c.offset, c.cursor, c.xi, c.v, c.P, c.vprev, c.id,
+                                                 c.xi_new, c.vnew, c.P_new, c.vit, c.id_tmp);
+    ++c.launches;
+    std::swap(c.xi, c.xi_new);
+    std::swap(c.v, c.vnew);
+    std::swap(c.P, c.P_new);
+    std::swap(c.vprev, c.vit);
+    std::swap(c.id, c.id_tmp);
+}
+
+void launch_unpermute(Ctx& c, const double* src, double* dst, double s0, double s1, double s2) {
+    k_unpermute<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.id, src, dst, s0, s1, s2);
+    ++c.launches;
+}
+
+void launch_permute_in(Ctx& c, const double* src, double* dst, double s0, double s1, double s2) {
+    k_permute_in<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.id, src, dst, s0, s1, s2);
+    ++c.launches;
+}
+
+}  // namespace pic

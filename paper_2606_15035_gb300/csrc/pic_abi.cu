@@ -1,0 +1,702 @@
+// C-ABI of the PIC library: context management and the host side of Algorithm 1.
+//
+// Every entry point validates its arguments, runs its device work on the context's
+// stream, converts CUDA failures and device status bits into a pic_status, and records a
+// one-line reason in ctx->err.  No entry point aborts.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "pic_internal.h"
+
+using namespace pic;
+
+struct pic_ctx {
+    Ctx c;
+    std::vector<std::pair<void*, size_t>> allocs;
+};
+
+namespace {
+
+pic_status fail(pic_ctx* ctx, pic_status s, const std::string& why) {
+    if (ctx) ctx->c.err = why;
+    return s;
+}
+
+void* dev_alloc(pic_ctx* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (ctx->c.has_alloc) {
+        p = ctx->c.alloc.alloc(bytes, (void*)ctx->c.stream, ctx->c.alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ctx->allocs.emplace_back(p, bytes);
+    return p;
+}
+
+void free_all(pic_ctx* ctx) {
+    for (auto& a : ctx->allocs) {
+        if (ctx->c.has_alloc) ctx->c.alloc.free(a.first, a.second, (void*)ctx->c.stream, ctx->c.alloc.user);
+        else cudaFree(a.first);
+    }
+    ctx->allocs.clear();
+    if (ctx->c.host_results) cudaFreeHost(ctx->c.host_results);
+    if (ctx->c.host_status) cudaFreeHost(ctx->c.host_status);
+    ctx->c.host_results = nullptr;
+    ctx->c.host_status = nullptr;
+}
+
+// Largest sin^2(2 pi m / n) over integer m, and the smallest positive one.
+void sin2_range(int n, double& mx, double& mn_pos) {
+    mx = 0.0;
+    mn_pos = 0.0;
+    for (int m = 0; m < n; ++m) {
+        double s = std::sin(2.0 * M_PI * m / n);
+        s = s * s;
+        if (s < 1e-24) continue;
+        mx = std::max(mx, s);
+        mn_pos = mn_pos == 0.0 ? s : std::min(mn_pos, s);
+    }
+}
+
+// Chebyshev schedule for a symmetric operator with spectrum in [lmin, lmax]: the three-term
+// recurrence coefficients and the step count that brings the error bound
+// 2 rho^k / (1 + rho^{2k}), rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), below eps.
+int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* beta, int cap) {
+    double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    if (delta <= 1e-14 * theta) {
+        alpha[0] = 0.0;
+        beta[0] = 1.0 / theta;
+        return 1;
+    }
+    double kap = lmax / lmin;
+    double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    int k = (int)std::ceil(std::log(2.0 / eps) / std::log(1.0 / rho)) + 1;
+    k = std::min(std::max(k, 1), cap);
+    double sigma = theta / delta;
+    double rprev = 1.0 / sigma;
+    alpha[0] = 0.0;
+    beta[0] = 1.0 / theta;
+    for (int j = 1; j < k; ++j) {
+        double r = 1.0 / (2.0 * sigma - rprev);
+        alpha[j] = r * rprev;
+        beta[j] = 2.0 * r / delta;
+        rprev = r;
+    }
+    return k;
+}
+
+pic_status check_cuda(pic_ctx* ctx, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+// ---- live profiling ----
+cudaEvent_t take_event(Ctx& c) {
+    if (!c.ev_pool.empty()) {
+        cudaEvent_t e = c.ev_pool.back();
+        c.ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one phase with events on the context stream when profiling is on.
+struct ProfScope {
+    Ctx& c;
+    int phase;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Ctx& c_, int ph) : c(c_), phase(ph) {
+        if (c.prof) {
+            e0 = take_event(c);
+            cudaEventRecord(e0, c.stream);
+        }
+    }
+    ~ProfScope() {
+        if (c.prof) {
+            cudaEvent_t e1 = take_event(c);
+            cudaEventRecord(e1, c.stream);
+            c.ev_pending.push_back({phase, {e0, e1}});
+        }
+    }
+};
+
+// After a stream synchronisation: fold the pending event pairs into the accumulators.
+void prof_resolve(Ctx& c) {
+    for (auto& pe : c.ev_pending) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+        switch (pe.first) {
+            case PH_PUSH: c.prof_acc.push_ms += ms; c.prof_acc.push_launches += 1; c.prof_acc.particle_pushes += c.np; break;
+            case PH_COMMIT: c.prof_acc.commit_ms += ms; c.prof_acc.commit_launches += 1; break;
+            case PH_SCATTER: c.prof_acc.scatter_ms += ms; c.prof_acc.scatter_launches += 1; break;
+            case PH_MESH: c.prof_acc.mesh_ms += ms; break;
+            case PH_SORT: c.prof_acc.sort_ms += ms; break;
+            default: break;
+        }
+        c.ev_pool.push_back(pe.second.first);
+        c.ev_pool.push_back(pe.second.second);
+    }
+    c.ev_pending.clear();
+}
+
+// Copy results + status to the host and wait.
+pic_status sync_results(pic_ctx* ctx, const char* where) {
+    Ctx& c = ctx->c;
+    cudaMemcpyAsync(c.host_results, c.results, sizeof(double) * NSLOT, cudaMemcpyDeviceToHost, c.stream);
+    cudaMemcpyAsync(c.host_status, c.dev_status, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    if (c.prof) prof_resolve(c);
+    pic_status s = check_cuda(ctx, where);
+    if (s != PIC_OK) return s;
+    int st = *c.host_status;
+    if (st & DEV_ERR_SEGMENTS)
+        return fail(ctx, PIC_ERR_SEGMENTS, std::string(where) + ": an orbit crossed more knots than supported in one step");
+    if (st & DEV_ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, std::string(where) + ": non-finite particle velocity");
+    return PIC_OK;
+}
+
+pic_status validate(const pic_config* cfg) {
+    for (int a = 0; a < 3; ++a)
+        if (cfg->n[a] < 1 || !(cfg->L[a] > 0.0)) return PIC_ERR_ARG;
+    if ((int64_t)cfg->n[0] * cfg->n[1] * cfg->n[2] >= (int64_t)1 << 31) return PIC_ERR_ARG;
+    if (!(cfg->dt > 0.0) || !(cfg->kappa > 0.0) || !(cfg->sigma1 > 0.0) || !(cfg->sigma2 > 0.0)) return PIC_ERR_ARG;
+    if (!(cfg->picard_tol > 0.0) || cfg->picard_max < 0) return PIC_ERR_ARG;
+    if (cfg->quadrature != PIC_QUAD_CLOSED && cfg->quadrature != PIC_QUAD_GAUSS) return PIC_ERR_ARG;
+    if (cfg->quadrature == PIC_QUAD_CLOSED && !cfg->split_orbit_at_knots) return PIC_ERR_ARG;
+    if (cfg->quadrature == PIC_QUAD_GAUSS && (cfg->nq < 1 || cfg->nq > 16)) return PIC_ERR_ARG;
+    if (cfg->precision != PIC_FP64) return PIC_ERR_ARG;
+    if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
+    return PIC_OK;
+}
+
+void setup_geometry(Ctx& c) {
+    c.m.n[0] = c.cfg.n[0];
+    c.m.n[1] = c.cfg.n[1];
+    c.m.n[2] = c.cfg.n[2];
+    c.m.ncell = (int64_t)c.cfg.n[0] * c.cfg.n[1] * c.cfg.n[2];
+    c.volume = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        c.H[a] = c.cfg.L[a] / c.cfg.n[a];
+        c.invH[a] = 1.0 / c.H[a];
+        c.volume *= c.cfg.L[a];
+    }
+    c.dV = c.H[0] * c.H[1] * c.H[2];
+    // CN Helmholtz operator I - a Delta_h: spectrum [1, 1 + a sum_a max sin^2 / H_a^2].
+    double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
+    double lmax = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        double mx, mn;
+        sin2_range(c.cfg.n[ax], mx, mn);
+        lmax += a * mx * c.invH[ax] * c.invH[ax];
+    }
+    c.cheb_iters = cheb_schedule(1.0, lmax, c.cfg.helmholtz_tol, c.cheb_alpha, c.cheb_beta, 1024);
+}
+
+#define ALLOC(ptr, type, count)                                                          \
+    do {                                                                                 \
+        (ptr) = (type*)dev_alloc(ctx, sizeof(type) * (size_t)(count));                   \
+        if (!(ptr)) return fail(ctx, PIC_ERR_OOM, "device allocation of " #ptr " failed"); \
+    } while (0)
+
+pic_status allocate(pic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    const int64_t np3 = 3 * std::max<int64_t>(c.np, 1), N = c.m.ncell;
+    ALLOC(c.xi, double, np3);
+    ALLOC(c.v, double, np3);
+    ALLOC(c.P, double, np3);
+    ALLOC(c.vprev, double, np3);
+    ALLOC(c.vit, double, np3);
+    ALLOC(c.vnew, double, np3);
+    ALLOC(c.xi_new, double, np3);
+    ALLOC(c.P_new, double, np3);
+    ALLOC(c.sort_tmp, double, np3);
+    ALLOC(c.creep_list, int32_t, std::max<int64_t>(c.np, 1));
+    ALLOC(c.creep_count, int, 1);
+    ALLOC(c.id, int64_t, std::max<int64_t>(c.np, 1));
+    ALLOC(c.id_tmp, int64_t, std::max<int64_t>(c.np, 1));
+    ALLOC(c.key, int32_t, std::max<int64_t>(c.np, 1));
+    ALLOC(c.count, int32_t, N);
+    ALLOC(c.offset, int32_t, N);
+    ALLOC(c.cursor, int32_t, N);
+    ALLOC(c.scan_tmp, int32_t, (N + 1023) / 1024 + 1);
+    ALLOC(c.F0, double, 4 * N);
+    ALLOC(c.W0, double, 4 * N);
+    ALLOC(c.rho0, double, N);
+    ALLOC(c.F1, double, 4 * N);
+    ALLOC(c.F1b, double, 4 * N);
+    ALLOC(c.W1, double, 4 * N);
+    ALLOC(c.rho1, double, N);
+    ALLOC(c.cheb_d, double, 4 * N);
+    ALLOC(c.rhs0, double, 4 * N);
+    ALLOC(c.rhs, double, 4 * N);
+    for (int k = 0; k < 3; ++k) ALLOC(c.J[k], double, 3 * N);
+    ALLOC(c.table, double, 12 * N);
+    ALLOC(c.partials, double, (size_t)NSLOT * MAX_BLOCKS);
+    ALLOC(c.results, double, NSLOT);
+    ALLOC(c.dev_status, int, 1);
+    if (cudaMallocHost(&c.host_results, sizeof(double) * NSLOT) != cudaSuccess ||
+        cudaMallocHost(&c.host_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PIC_ERR_OOM, "pinned host allocation failed");
+    }
+    cudaMemsetAsync(c.partials, 0, sizeof(double) * (size_t)NSLOT * MAX_BLOCKS, c.stream);
+    cudaMemsetAsync(c.results, 0, sizeof(double) * NSLOT, c.stream);
+    cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
+    return check_cuda(ctx, "allocate");
+}
+
+// -Delta_h phi = sigma1 rho on the non-null modes by Chebyshev iteration (rho projected).
+pic_status solve_poisson(pic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    const int64_t N = c.m.ncell;
+    double lmax = 0.0, lmin = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        double mx, mn;
+        sin2_range(c.cfg.n[ax], mx, mn);
+        lmax += mx * c.invH[ax] * c.invH[ax];
+        if (mn > 0.0) {
+            double v = mn * c.invH[ax] * c.invH[ax];
+            lmin = lmin == 0.0 ? v : std::min(lmin, v);
+        }
+    }
+    // (0 I - (1/sigma1) Delta_h) phi = rho  <=>  -Delta_h phi = sigma1 rho; initial guess 0
+    cudaMemcpyAsync(c.rhs, c.rho0, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream);
+    launch_fill(c, c.F0, N, 0.0);
+    if (lmin > 0.0) {
+        std::vector<double> al(4096), be(4096);
+        int it = cheb_schedule(lmin / c.cfg.sigma1, lmax / c.cfg.sigma1, c.cfg.helmholtz_tol, al.data(), be.data(), 4096);
+        double* x = c.F0;
+        double* spare = c.F1b;
+        launch_helmholtz(c, c.rhs, 0.0, 1.0 / c.cfg.sigma1, 1, it, al.data(), be.data(), &x, &spare);
+        if (x != c.F0) cudaMemcpyAsync(c.F0, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream);
+        launch_null_project(c, c.F0, 0.0);
+    }
+    return check_cuda(ctx, "poisson");
+}
+
+}  // namespace
+
+
+namespace {
+
+// Energy of the current state into results[S_K], results[S_W0].
+void queue_energy(Ctx& c) {
+    launch_kinetic(c);
+    launch_finalize(c, S_K, 1, particle_blocks(c), false);
+    launch_mesh_energy(c, c.F0, c.W0, S_W0);
+    launch_finalize(c, S_W0, 1, mesh_blocks(c), false);
+}
+
+// The mesh half of one Algorithm 1 iteration: continuity, CN solve (warm-started from F1),
+// back-substitution and the gather table.
+void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev) {
+    const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
+    ProfScope ps(c, PH_MESH);
+    launch_source(c, Jcur, Jprev);
+    launch_helmholtz(c, c.rhs, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, &c.F1, &c.F1b);
+    launch_backsub_table(c, false);
+}
+
+// One time step.  On failure nothing of the committed state (F0, W0, rho0, xi, v, P, vprev)
+// has changed except the particle order, which get_state undoes.
+pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
+    Ctx& c = ctx->c;
+    const int64_t N = c.m.ncell, np = c.np;
+    const bool diag = c.cfg.diagnostics != 0;
+    if (np > 0 && c.cfg.sort_every > 0 && c.steps % c.cfg.sort_every == 0) {
+        ProfScope ps(c, PH_SORT);
+        launch_sort(c);
+    }
+    if (diag) queue_energy(c);
+    launch_rhs0(c);
+    cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
+    int cur = 0, prev = 1, next = 2;
+    cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
+    {
+        ProfScope ps(c, PH_SCATTER);
+        launch_first_scatter(c, c.J[cur], nullptr);
+    }
+    launch_finalize(c, S_JSCALE, 1, particle_blocks(c), false);
+    bool converged = false;
+    double e_v = 0.0, e_J = 0.0, jscale = 0.0;
+    int p = 0;
+    for (p = 0; p <= c.cfg.picard_max; ++p) {
+        mesh_phase(c, c.J[cur], p > 0 ? c.J[prev] : nullptr);
+        cudaMemsetAsync(c.J[next], 0, sizeof(double) * 3 * N, c.stream);
+        {
+            ProfScope ps(c, PH_PUSH);
+            launch_push(c, c.vit, c.vnew, c.J[next], false, false);
+        }
+        launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
+        launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
+        if (c.prof) launch_finalize(c, S_PIECES_PUSH, 2, particle_blocks(c), false);
+        pic_status s = sync_results(ctx, "pic_step");
+        if (s != PIC_OK) return s;
+        const double* r = c.host_results;
+        if (c.prof) {
+            c.prof_acc.push_pieces += (int64_t)r[S_PIECES_PUSH];
+            c.prof_acc.scatter_pieces += (int64_t)r[S_PIECES_SCATTER];
+        }
+        if (p == 0) jscale = std::sqrt((double)N) * std::fabs(c.q) * r[S_JSCALE] / c.volume;
+        e_v = r[S_EV_DEN] > 0.0 ? std::sqrt(r[S_EV_NUM] / r[S_EV_DEN]) : 0.0;
+        {
+            double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
+            e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
+        }
+        if (!std::isfinite(e_v) || (p > 0 && !std::isfinite(e_J)))
+            return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
+        if (e_v <= c.cfg.picard_tol && e_J <= c.cfg.picard_tol) {
+            converged = true;
+            break;
+        }
+        if (p == c.cfg.picard_max) break;
+        std::swap(c.vit, c.vnew);
+        int old_prev = prev;
+        prev = cur;
+        cur = next;
+        next = old_prev;
+    }
+    if (last) {
+        last->iterations = std::min(p, c.cfg.picard_max) + 1;
+        last->converged = converged ? 1 : 0;
+        last->e_v = e_v;
+        last->e_J = e_J;
+    }
+    if (!converged && !c.cfg.accept_unconverged) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "pic_step: Picard not converged after %d iterations (e_v=%.3e, e_J=%.3e)",
+                      c.cfg.picard_max + 1, e_v, e_J);
+        return fail(ctx, PIC_ERR_NO_CONVERGENCE, buf);
+    }
+    // Final consistency sweep (§5.4): orbit of v^{n+1,p+1}, whose current is in J[next].
+    std::swap(c.vit, c.vnew);
+    double* Jfin = c.J[next];
+    mesh_phase(c, Jfin, nullptr);
+    {
+        ProfScope ps(c, PH_COMMIT);
+        launch_push(c, c.vit, c.vnew, nullptr, true, diag);
+    }
+    if (diag) {
+        launch_finalize(c, S_K1, 3, particle_blocks(c), false);   // K1, PWORK, RA_SQ
+        launch_finalize(c, S_RA_MAX, 2, particle_blocks(c), true);
+        launch_mesh_diag(c, Jfin);
+        launch_finalize(c, S_MWORK, 2, mesh_blocks(c), false);    // MWORK, W
+        launch_finalize(c, S_G_MAX, 1, mesh_blocks(c), true);
+        launch_finalize(c, S_G_SQ, 1, mesh_blocks(c), false);
+        launch_finalize(c, S_R_MAX, 1, mesh_blocks(c), true);
+        launch_finalize(c, S_R_SQ, 1, mesh_blocks(c), false);
+        launch_finalize(c, S_CONT_MAX, 1, mesh_blocks(c), true);
+    }
+    pic_status s = sync_results(ctx, "pic_step final sweep");
+    if (s != PIC_OK) return s;
+    // commit: level n+1 becomes level n; v^{n-1} <- v^n
+    std::swap(c.F0, c.F1);
+    std::swap(c.W0, c.W1);
+    std::swap(c.rho0, c.rho1);
+    std::swap(c.xi, c.xi_new);
+    std::swap(c.P, c.P_new);
+    std::swap(c.vprev, c.v);
+    std::swap(c.v, c.vnew);
+    c.steps += 1;
+    if (diag) {
+        const double* r = c.host_results;
+        pic_diag_t& d = c.diag;
+        const double dt = c.cfg.dt;
+        d.K0 = r[S_K];
+        d.W0 = r[S_W0];
+        d.K1 = r[S_K1];
+        d.W1 = r[S_W];
+        d.particle_work = r[S_PWORK];
+        d.mesh_work = r[S_MWORK];
+        d.R_field = d.W1 - d.W0 + dt * d.mesh_work;
+        d.R_particle = d.K1 - d.K0 - dt * d.particle_work;
+        d.R_total = (d.K1 + d.W1) - (d.K0 + d.W0);
+        d.RA_max = r[S_RA_MAX];
+        d.RA_rms = np > 0 ? std::sqrt(r[S_RA_SQ] / (3.0 * np)) : 0.0;
+        d.partition_max = r[S_PU_MAX];
+        d.gauge_max = r[S_G_MAX];
+        d.gauge_rms = std::sqrt(r[S_G_SQ] / (double)N);
+        d.gauss_max = r[S_R_MAX];
+        d.gauss_rms = std::sqrt(r[S_R_SQ] / (double)N);
+        d.continuity_max = r[S_CONT_MAX];
+        d.picard_iterations = std::min(p, c.cfg.picard_max) + 1;
+        d.e_v = e_v;
+        d.e_J = e_J;
+        c.have_diag = true;
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_config_default(pic_config* cfg) {
+    if (!cfg) return PIC_ERR_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    const double side = 2.0 * M_PI / 3.0;
+    for (int a = 0; a < 3; ++a) {
+        cfg->n[a] = 8;
+        cfg->L[a] = side;
+    }
+    cfg->dt = 0.1;
+    cfg->kappa = cfg->sigma1 = cfg->sigma2 = 1.0;
+    cfg->n0 = 1.0;
+    cfg->picard_tol = 1e-13;
+    cfg->picard_max = 16;
+    cfg->split_orbit_at_knots = 1;
+    cfg->quadrature = PIC_QUAD_CLOSED;
+    cfg->nq = 16;
+    cfg->precision = PIC_FP64;
+    cfg->sort_every = 1;
+    cfg->diagnostics = 0;
+    cfg->accept_unconverged = 0;
+    cfg->picard_accel = 1;
+    cfg->helmholtz_tol = 1e-17;
+    return PIC_OK;
+}
+
+pic_status pic_init(const pic_config* cfg, const pic_particles* particles, const pic_allocator* alloc, void* stream,
+                    pic_ctx** out) {
+    if (!cfg || !particles || !out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (validate(cfg) != PIC_OK) return PIC_ERR_ARG;
+    if (particles->np < 0 || (particles->np > 0 && (!particles->x || !particles->v)) || !(particles->m > 0.0))
+        return PIC_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return PIC_ERR_ARG;
+    pic_ctx* ctx = new (std::nothrow) pic_ctx();
+    if (!ctx) return PIC_ERR_OOM;
+    Ctx& c = ctx->c;
+    c.cfg = *cfg;
+    c.stream = (cudaStream_t)stream;
+    if (alloc) {
+        c.alloc = *alloc;
+        c.has_alloc = true;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return PIC_ERR_CUDA;
+    }
+    c.np = particles->np;
+    c.q = particles->q;
+    c.mass = particles->m;
+    setup_geometry(c);
+    pic_status s = allocate(ctx);
+    if (s != PIC_OK) {
+        free_all(ctx);
+        delete ctx;
+        return s;
+    }
+    if (cfg->quadrature == PIC_QUAD_GAUSS) set_gauss_rule(cfg->nq);
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kind = particles->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (np > 0) {
+        // positions to the scratch buffer, then wrapped cell units; velocities straight in
+        cudaMemcpyAsync(c.sort_tmp, particles->x, sizeof(double) * 3 * np, kind, c.stream);
+        cudaMemcpyAsync(c.v, particles->v, sizeof(double) * 3 * np, kind, c.stream);
+        launch_init_positions(c, c.sort_tmp);
+        if (c.cfg.sort_every > 0) {
+            cudaMemcpyAsync(c.vprev, c.v, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
+            cudaMemcpyAsync(c.P, c.v, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
+            launch_sort(c);
+        }
+    }
+    // rho^0 = sum q S / dV + n0, null modes removed; phi^0 from Poisson; psi = A = U = 0
+    launch_fill(c, c.rho0, N, 0.0);
+    if (np > 0) launch_point_deposit(c);
+    launch_null_project(c, c.rho0, c.cfg.n0);
+    s = solve_poisson(ctx);
+    if (s == PIC_OK) {
+        launch_fill(c, c.F0 + N, 3 * N, 0.0);
+        launch_fill(c, c.W0, 4 * N, 0.0);
+        if (np > 0) {
+            // v^{n-1} = v^0 and P = m v + q A_h(x) = m v since A^0 = 0
+            cudaMemcpyAsync(c.vprev, c.v, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
+            launch_scale_copy(c, c.P, c.v, 3 * np, c.mass);
+        }
+    }
+    if (s == PIC_OK) s = sync_results(ctx, "pic_init");
+    if (s != PIC_OK) {
+        free_all(ctx);
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return PIC_OK;
+}
+
+
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps, pic_step_info* info) {
+    if (!ctx || nsteps < 0) return PIC_ERR_ARG;
+    ctx->c.err.clear();
+    pic_step_info local{};
+    pic_step_info last{};
+    pic_status s = PIC_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        s = run_step(ctx, &last);
+        if (s != PIC_OK) break;
+        local.steps_done += 1;
+        local.total_iterations += last.iterations;
+    }
+    local.iterations = last.iterations;
+    local.converged = last.converged;
+    local.e_v = last.e_v;
+    local.e_J = last.e_J;
+    if (info) *info = local;
+    return s;
+}
+
+pic_status pic_energy(pic_ctx* ctx, pic_energy_t* out) {
+    if (!ctx || !out) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    queue_energy(c);
+    pic_status s = sync_results(ctx, "pic_energy");
+    if (s != PIC_OK) return s;
+    out->K = c.host_results[S_K];
+    out->W = c.host_results[S_W0];
+    out->total = out->K + out->W;
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics(pic_ctx* ctx, pic_diag_t* out) {
+    if (!ctx || !out) return PIC_ERR_ARG;
+    if (!ctx->c.have_diag) return fail(ctx, PIC_ERR_ARG, "pic_diagnostics: no step with diagnostics = 1 has run");
+    *out = ctx->c.diag;
+    return PIC_OK;
+}
+
+pic_status pic_get_state(pic_ctx* ctx, const pic_state_view* dst) {
+    if (!ctx || !dst) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kind = dst->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (np > 0) {
+        double* outs[4] = {dst->x, dst->v, dst->P, dst->vprev};
+        const double* srcs[4] = {c.xi, c.v, c.P, c.vprev};
+        for (int k = 0; k < 4; ++k) {
+            if (!outs[k]) continue;
+            double sc[3] = {1.0, 1.0, 1.0};
+            if (k == 0) sc[0] = c.H[0], sc[1] = c.H[1], sc[2] = c.H[2];
+            launch_unpermute(c, srcs[k], c.sort_tmp, sc[0], sc[1], sc[2]);
+            cudaMemcpyAsync(outs[k], c.sort_tmp, sizeof(double) * 3 * np, kind, c.stream);
+        }
+    }
+    if (dst->phi) cudaMemcpyAsync(dst->phi, c.F0, sizeof(double) * N, kind, c.stream);
+    if (dst->A) cudaMemcpyAsync(dst->A, c.F0 + N, sizeof(double) * 3 * N, kind, c.stream);
+    if (dst->psi) cudaMemcpyAsync(dst->psi, c.W0, sizeof(double) * N, kind, c.stream);
+    if (dst->U) cudaMemcpyAsync(dst->U, c.W0 + N, sizeof(double) * 3 * N, kind, c.stream);
+    if (dst->rho) cudaMemcpyAsync(dst->rho, c.rho0, sizeof(double) * N, kind, c.stream);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_state");
+    return check_cuda(ctx, "pic_get_state");
+}
+
+pic_status pic_set_state(pic_ctx* ctx, const pic_state_view* src) {
+    if (!ctx || !src) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    const int64_t np = c.np, N = c.m.ncell;
+    if (np > 0 && (!src->x || !src->v || !src->P || !src->vprev)) return PIC_ERR_ARG;
+    if (!src->phi || !src->psi || !src->rho || !src->A || !src->U) return PIC_ERR_ARG;
+    const cudaMemcpyKind kind = src->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (np > 0) {
+        // the given order becomes the device order (identity permutation)
+        cudaMemcpyAsync(c.sort_tmp, src->x, sizeof(double) * 3 * np, kind, c.stream);
+        launch_init_positions(c, c.sort_tmp);
+        cudaMemcpyAsync(c.v, src->v, sizeof(double) * 3 * np, kind, c.stream);
+        cudaMemcpyAsync(c.P, src->P, sizeof(double) * 3 * np, kind, c.stream);
+        cudaMemcpyAsync(c.vprev, src->vprev, sizeof(double) * 3 * np, kind, c.stream);
+    }
+    cudaMemcpyAsync(c.F0, src->phi, sizeof(double) * N, kind, c.stream);
+    cudaMemcpyAsync(c.F0 + N, src->A, sizeof(double) * 3 * N, kind, c.stream);
+    cudaMemcpyAsync(c.W0, src->psi, sizeof(double) * N, kind, c.stream);
+    cudaMemcpyAsync(c.W0 + N, src->U, sizeof(double) * 3 * N, kind, c.stream);
+    cudaMemcpyAsync(c.rho0, src->rho, sizeof(double) * N, kind, c.stream);
+    c.have_diag = false;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_set_state");
+    return check_cuda(ctx, "pic_set_state");
+}
+
+pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, const pic_iterate_out* out) {
+    if (!ctx || !v_iter || !out) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    double* vgiven = nullptr;
+    if (np > 0) {
+        cudaMemcpyAsync(c.vnew, v_iter, sizeof(double) * 3 * np, kin, c.stream);
+        launch_permute_in(c, c.vnew, c.sort_tmp, 1.0, 1.0, 1.0);   // caller order -> device order
+        vgiven = c.sort_tmp;
+    }
+    launch_rhs0(c);
+    cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
+    cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
+    if (np > 0) launch_first_scatter(c, c.J[0], vgiven);
+    mesh_phase(c, c.J[0], nullptr);
+    if (np > 0) launch_push(c, c.vit, c.vnew, nullptr, true, false);
+    pic_status s = sync_results(ctx, "pic_iterate");
+    if (s != PIC_OK) return s;
+    if (out->J) cudaMemcpyAsync(out->J, c.J[0], sizeof(double) * 3 * N, kout, c.stream);
+    if (out->rho) cudaMemcpyAsync(out->rho, c.rho1, sizeof(double) * N, kout, c.stream);
+    if (out->phi) cudaMemcpyAsync(out->phi, c.F1, sizeof(double) * N, kout, c.stream);
+    if (out->A) cudaMemcpyAsync(out->A, c.F1 + N, sizeof(double) * 3 * N, kout, c.stream);
+    if (out->psi) cudaMemcpyAsync(out->psi, c.W1, sizeof(double) * N, kout, c.stream);
+    if (out->U) cudaMemcpyAsync(out->U, c.W1 + N, sizeof(double) * 3 * N, kout, c.stream);
+    if (np > 0) {
+        double* outs[3] = {out->x, out->P, out->v};
+        const double* srcs[3] = {c.xi_new, c.P_new, c.vnew};
+        for (int k = 0; k < 3; ++k) {
+            if (!outs[k]) continue;
+            double sc[3] = {1.0, 1.0, 1.0};
+            if (k == 0) sc[0] = c.H[0], sc[1] = c.H[1], sc[2] = c.H[2];
+            launch_unpermute(c, srcs[k], c.sort_tmp, sc[0], sc[1], sc[2]);
+            cudaMemcpyAsync(outs[k], c.sort_tmp, sizeof(double) * 3 * np, kout, c.stream);
+        }
+    }
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_iterate");
+    return check_cuda(ctx, "pic_iterate");
+}
+
+pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out) {
+    if (!ctx) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_profile");
+    prof_resolve(c);
+    if (out) {
+        *out = c.prof_acc;
+        out->launches = c.launches;
+        c.prof_acc = pic_profile_t{};
+        c.launches = 0;
+    }
+    c.prof = enable != 0;
+    return check_cuda(ctx, "pic_profile");
+}
+
+const char* pic_last_error(const pic_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->c.err.c_str();
+}
+
+void pic_destroy(pic_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->c.stream);
+    prof_resolve(ctx->c);
+    for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Device-side building blocks of the orbit-averaged particle step (sm_103a).
+//
+// Positions are carried in cell units (xi = x / H per axis), so the knots of the
+// tensor-product linear B-spline (r = 1, the shape of the paper's §5.4 test) are the
+// integers and the mesh node g sits at integer coordinates.  A particle orbit over one
+// step is the straight segment xi(s) = xi0 + s * beta, 0 <= s <= 1, with beta the
+// unwrapped displacement in cell units (§4.2, Eq. (particle-orbit)).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+// Error bits set in the device status word (read by the host at sync points).
+enum : int {
+    DEV_ERR_SEGMENTS = 1,   // more knot crossings in one step than MAX_SEGMENTS allows
+    DEV_ERR_NONFINITE = 2,  // a non-finite velocity or residual appeared
+};
+
+constexpr int MAX_SEGMENTS = 64;
+
+struct MeshDims {
+    int n[3];       // nodes per axis
+    int64_t ncell;  // n0 * n1 * n2
+};
+
+__device__ __forceinline__ int wrapi(int c, int n) {
+    int r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+// Row index of node (ix, iy, iz) in the x-fastest mesh layout.
+__device__ __forceinline__ int64_t node_index(int ix, int iy, int iz, const MeshDims& m) {
+    return (int64_t)ix + (int64_t)m.n[0] * ((int64_t)iy + (int64_t)m.n[1] * iz);
+}
+
+template <typename T>
+__device__ __forceinline__ T wrap_pos(T x, T n) {
+    T w = x - n * floor(x / n);
+    return w >= n ? w - n : w;
+}
+
+// One knot-free piece [s0, s0 + h] of an orbit: the stencil cell containing its midpoint
+// and the normalised start coordinate r_{a,m} in that cell (Appendix A).
+template <typename T>
+struct Segment {
+    T s0, h;
+    int cell[3];
+    T r[3];
+};
+
+// Visit the pieces of the orbit xi0 + s * beta between consecutive breakpoints.
+// The breakpoints are {0, 1} and every s in (0, 1) at which some axis crosses a knot
+// (§4.7, Eq. (breakpoint-set)); the three per-axis crossing sequences are already
+// sorted, so they are merged on the fly.  Coincident crossings produce one breakpoint;
+// an axis with beta_a = 0 contributes none.  With split = false the whole path [0, 1]
+// is one piece; that form is only used with the Gauss rule (the unsplit comparison run
+// of §5.4), whose samples find their own cell, so seg.cell / seg.r are not used then.
+// Returns the number of pieces, or -1 if MAX_SEGMENTS was exceeded.
+template <typename T, typename F>
+__device__ __forceinline__ int for_each_segment(const T xi0[3], const T beta[3], bool split, F&& visit) {
+    T snext[3], knot[3], step[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        snext[a] = T(2);
+        knot[a] = T(0);
+        step[a] = T(0);
+        if (split && beta[a] > T(0)) {
+            knot[a] = floor(xi0[a]) + T(1);
+            step[a] = T(1);
+            snext[a] = (knot[a] - xi0[a]) / beta[a];
+        } else if (split && beta[a] < T(0)) {
+            knot[a] = ceil(xi0[a]) - T(1);
+            step[a] = T(-1);
+            snext[a] = (knot[a] - xi0[a]) / beta[a];
+        }
+        if (!(snext[a] < T(1))) snext[a] = T(2);
+    }
+    T s0 = T(0);
+    for (int it = 0; it < MAX_SEGMENTS; ++it) {
+        T s1 = fmin(fmin(snext[0], snext[1]), fmin(snext[2], T(1)));
+        T h = s1 - s0;
+        if (h > T(0)) {
+            Segment<T> seg;
+            seg.s0 = s0;
+            seg.h = h;
+            T mid = T(0.5) * (s0 + s1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                T c = floor(xi0[a] + mid * beta[a]);
+                seg.cell[a] = (int)c;
+                seg.r[a] = xi0[a] + s0 * beta[a] - c;
+            }
+            visit(seg);
+        }
+        if (s1 >= T(1)) return it + 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (snext[a] == s1) {
+                knot[a] += step[a];
+                T sn = (knot[a] - xi0[a]) / beta[a];
+                snext[a] = sn < T(1) ? sn : T(2);
+            }
+        }
+        s0 = s1;
+    }
+    return -1;
+}
+
+// Per-axis linear weights on a piece: w_{a,0}(eta) = L0 + M0 eta, w_{a,1} = L1 + M1 eta,
+// with L0 = 1 - r, M0 = -beta, L1 = r, M1 = beta (Appendix A).
+template <typename T>
+struct AxisPoly {
+    T L[2], M[2];
+};
+
+template <typename T>
+__device__ __forceinline__ AxisPoly<T> axis_poly(T r, T beta) {
+    AxisPoly<T> p;
+    p.L[0] = T(1) - r;
+    p.M[0] = -beta;
+    p.L[1] = r;
+    p.M[1] = beta;
+    return p;
+}
+
+// Quadratic product (La + Ma eta)(Lb + Mb eta) = d0 + d1 eta + d2 eta^2.
+template <typename T>
+struct Quad {
+    T d0, d1, d2;
+};
+
+template <typename T>
+__device__ __forceinline__ Quad<T> quad_product(T La, T Ma, T Lb, T Mb) {
+    Quad<T> q;
+    q.d0 = La * Lb;
+    q.d1 = Ma * Lb + La * Mb;
+    q.d2 = Ma * Mb;
+    return q;
+}
+
+// I_nu = int_0^h (c0 + c1 eta + c2 eta^2 + c3 eta^3) d eta with the cubic being the
+// product of a quadratic (two axes) and a linear factor (third axis) (Appendix A).
+template <typename T>
+__device__ __forceinline__ T segment_weight(const Quad<T>& q, T L, T M, T h) {
+    T c0 = q.d0 * L;
+    T c1 = q.d1 * L + q.d0 * M;
+    T c2 = q.d2 * L + q.d1 * M;
+    T c3 = q.d2 * M;
+    return h * (c0 + h * (c1 * T(0.5) + h * (c2 * (T(1) / T(3)) + h * (c3 * T(0.25)))));
+}
+
+// The two bracketed integrals of I^D (Appendix B) for a transverse quadratic d:
+// T0 = int_0^h d(eta) d eta, T1 = int_0^h eta d(eta) d eta.
+template <typename T>
+__device__ __forceinline__ void transverse_integrals(const Quad<T>& q, T h, T& t0, T& t1) {
+    t0 = h * (q.d0 + h * (q.d1 * T(0.5) + h * (q.d2 * (T(1) / T(3)))));
+    t1 = h * h * (q.d0 * T(0.5) + h * (q.d1 * (T(1) / T(3)) + h * (q.d2 * T(0.25))));
+}
+
+// Eight closed-form weights I_nu of one piece, nu = nx + 2 ny + 4 nz (Appendix A).
+template <typename T>
+__device__ __forceinline__ void segment_weights8(const Segment<T>& sg, const T beta[3], T I[8]) {
+    AxisPoly<T> px = axis_poly(sg.r[0], beta[0]);
+    AxisPoly<T> py = axis_poly(sg.r[1], beta[1]);
+    AxisPoly<T> pz = axis_poly(sg.r[2], beta[2]);
+#pragma unroll
+    for (int ny = 0; ny < 2; ++ny)
+#pragma unroll
+        for (int nx = 0; nx < 2; ++nx) {
+            Quad<T> qxy = quad_product(px.L[nx], px.M[nx], py.L[ny], py.M[ny]);
+#pragma unroll
+            for (int nz = 0; nz < 2; ++nz) I[nx + 2 * ny + 4 * nz] = segment_weight(qxy, pz.L[nz], pz.M[nz], sg.h);
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void segment_nodes8(const Segment<T>& sg, const MeshDims& m, int64_t g[8]) {
+    int x0 = wrapi(sg.cell[0], m.n[0]), x1 = wrapi(sg.cell[0] + 1, m.n[0]);
+    int y0 = wrapi(sg.cell[1], m.n[1]), y1 = wrapi(sg.cell[1] + 1, m.n[1]);
+    int z0 = wrapi(sg.cell[2], m.n[2]), z1 = wrapi(sg.cell[2] + 1, m.n[2]);
+    g[0] = node_index(x0, y0, z0, m);
+    g[1] = node_index(x1, y0, z0, m);
+    g[2] = node_index(x0, y1, z0, m);
+    g[3] = node_index(x1, y1, z0, m);
+    g[4] = node_index(x0, y0, z1, m);
+    g[5] = node_index(x1, y0, z1, m);
+    g[6] = node_index(x0, y1, z1, m);
+    g[7] = node_index(x1, y1, z1, m);
+}
+
+// Point value of the 8 linear B-splines around a wrapped position (Eq. (Ah-mesh)).
+template <typename T>
+__device__ __forceinline__ void point_weights8(const T xi[3], const MeshDims& m, int64_t g[8], T w[8]) {
+    int c[3];
+    T r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T f = floor(xi[a]);
+        c[a] = (int)f;
+        r[a] = xi[a] - f;
+    }
+    Segment<T> sg;
+    sg.cell[0] = c[0];
+    sg.cell[1] = c[1];
+    sg.cell[2] = c[2];
+    segment_nodes8(sg, m, g);
+#pragma unroll
+    for (int nz = 0; nz < 2; ++nz)
+#pragma unroll
+        for (int ny = 0; ny < 2; ++ny)
+#pragma unroll
+            for (int nx = 0; nx < 2; ++nx) {
+                T wx = nx ? r[0] : T(1) - r[0];
+                T wy = ny ? r[1] : T(1) - r[1];
+                T wz = nz ? r[2] : T(1) - r[2];
+                w[nx + 2 * ny + 4 * nz] = wx * wy * wz;
+            }
+}
+
+// ---- block reductions (fixed order, so results are reproducible for a fixed launch) ----
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  blockDim.x <= 1024.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* smem32) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem32[wid] = v;
+    __syncthreads();
+    T r = T(0);
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? smem32[lane] : T(0);
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* smem32) {
+    v = warp_max(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem32[wid] = v;
+    __syncthreads();
+    T r = T(0);
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? smem32[lane] : T(0);
+        r = warp_max(r);
+    }
+    return r;
+}
+
+}  // namespace pic

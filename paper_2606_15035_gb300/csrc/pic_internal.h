@@ -1,0 +1,142 @@
+// Host-side context and kernel launchers of the PIC library (internal).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pic.h"
+#include "pic_device.cuh"
+
+namespace pic {
+
+// Reduction slots: each kernel writes one partial per block into partials[slot * MAX_BLOCKS + b];
+// finalize() folds them in a fixed order into results[slot].
+enum Slot : int {
+    S_EV_NUM = 0,  // sum |v^{p+1} - v^p|^2
+    S_EV_DEN,      // sum |v^{p+1}|^2
+    S_EJ_NUM,      // sum |J^p - J^{p-1}|^2
+    S_EJ_DEN,      // sum |J^p|^2
+    S_JSCALE,      // sum |v^n|
+    S_K1,          // sum m |v^{n+1}|^2 / 2
+    S_PWORK,       // sum q vbar . Ebar
+    S_RA_SQ,       // sum |R_A|^2
+    S_RA_MAX,      // max |R_A| (component)
+    S_PU_MAX,      // max |sum Sbar - 1|
+    S_MWORK,       // sum J . E^{n+1/2} dV
+    S_W,           // field energy at n+1 (diagnostics)
+    S_W0,          // field energy of the current state
+    S_G_MAX,
+    S_G_SQ,
+    S_R_MAX,
+    S_R_SQ,
+    S_CONT_MAX,
+    S_K,           // kinetic energy of the current state
+    S_PIECES_PUSH,     // orbit pieces visited by the push (profiling)
+    S_PIECES_SCATTER,  // orbit pieces visited by the scatter of the next orbit (profiling)
+    S_PROJ0,       // 8 null-mode projections (init)
+    S_NULLSTAT = S_PROJ0 + 8,
+    NSLOT
+};
+
+constexpr int MAX_BLOCKS = 4096;
+constexpr int THREADS = 256;
+
+struct StepParams {
+    MeshDims m;
+    double H[3], invH[3];
+    double dt, q, mass, q_dV;  // q_dV = q / dV
+    int64_t np;
+    int split;                 // split orbits at knots
+    int nq;                    // Gauss points (Gauss quadrature only)
+    int accel;                 // particle-local solves for creeping particles
+};
+
+struct Ctx {
+    pic_config cfg;
+    cudaStream_t stream = nullptr;
+    pic_allocator alloc{};
+    bool has_alloc = false;
+    std::string err;
+
+    MeshDims m{};
+    int sms = 152;
+    double H[3], invH[3], dV = 0, volume = 0;
+    int64_t np = 0;
+    double q = 0, mass = 0;
+
+    // particles, FP64 SoA (3 * np each)
+    double *xi = nullptr, *v = nullptr, *P = nullptr, *vprev = nullptr;
+    double *vit = nullptr, *vnew = nullptr, *xi_new = nullptr, *P_new = nullptr;
+    int32_t* creep_list = nullptr;   // creeping particles of the current iteration (local solves)
+    int* creep_count = nullptr;
+    int64_t *id = nullptr, *id_tmp = nullptr;
+    double* sort_tmp = nullptr;          // 3 * np
+    int32_t *key = nullptr, *count = nullptr, *offset = nullptr, *cursor = nullptr;
+    int32_t* scan_tmp = nullptr;         // block totals of the scan
+
+    // mesh, FP64.  F = [phi | A_x | A_y | A_z] and W = [psi | U_x | U_y | U_z] (4 * ncell).
+    double *F0 = nullptr, *W0 = nullptr, *rho0 = nullptr;
+    double *F1 = nullptr, *F1b = nullptr, *W1 = nullptr, *rho1 = nullptr;
+    double *cheb_d = nullptr, *rhs0 = nullptr, *rhs = nullptr;
+    double *J[3] = {nullptr, nullptr, nullptr};
+    double* table = nullptr;             // 12 * ncell gather table
+
+    // reductions and status
+    double *partials = nullptr, *results = nullptr;
+    int* dev_status = nullptr;
+    double* host_results = nullptr;      // pinned, NSLOT
+    int* host_status = nullptr;          // pinned
+
+    // Chebyshev schedule for the CN Helmholtz solve
+    int cheb_iters = 0;
+    double cheb_alpha[1024], cheb_beta[1024];
+
+    // live profiling: event pairs per phase, resolved at the next stream synchronisation
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    pic_profile_t prof_acc{};
+    int64_t launches = 0;
+
+    // bookkeeping
+    int64_t steps = 0;
+    bool have_diag = false;
+    pic_diag_t diag{};
+    bool have_energy = false;
+    double K_n = 0, W_n = 0;
+};
+
+enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT };
+
+// ---- launchers (particles.cu) ----
+void launch_init_positions(Ctx& c, const double* x_dev);
+void launch_point_deposit(Ctx& c);
+void launch_sort(Ctx& c);
+void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null);
+void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag);
+void launch_kinetic(Ctx& c);
+void launch_unpermute(Ctx& c, const double* src_soa3, double* dst_soa3, double scale0, double scale1, double scale2);
+void launch_permute_in(Ctx& c, const double* src_soa3, double* dst_soa3, double s0, double s1, double s2);
+void set_gauss_rule(int nq);
+
+// ---- launchers (mesh.cu) ----
+void launch_rhs0(Ctx& c);
+void launch_source(Ctx& c, const double* Jcur, const double* Jprev);
+void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nfields, int iters,
+                      const double* alpha, const double* beta, double** x_io, double** x_spare);
+void launch_backsub_table(Ctx& c, bool diag);
+void launch_null_project(Ctx& c, double* f, double add_const);
+void launch_mesh_energy(Ctx& c, const double* F, const double* W, int slot);
+void launch_mesh_diag(Ctx& c, const double* Jfinal);
+void launch_finalize(Ctx& c, int slot0, int nslots, int nblocks, bool is_max);
+void launch_fill(Ctx& c, double* p, int64_t n, double value);
+void launch_scale_copy(Ctx& c, double* dst, const double* src, int64_t n, double s);
+
+int particle_blocks(const Ctx& c);
+int mesh_blocks(const Ctx& c);
+
+}  // namespace pic

@@ -1,0 +1,323 @@
+"""GPU parity: the sm_103a library (through its C-ABI) against the FP64 CPU oracle.
+
+Same seeded inputs on both sides; element-by-element comparison of mesh fields and
+particles.  Tolerance: relative L2 <= 1e-12 for FP64 state (the FP64 target), tighter
+where the computation is shallow (one iteration, initial data).  Positions are compared
+modulo the box.  The full-size case uses the 32^3 x 2,097,152-particle workload: the
+orbit current and mesh update in full, the particle push on a sample of particles.
+"""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import mesh as omesh
+from oracle import pic as opic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim(cuda_ok):
+    from paper_2606_15035_gb300 import build
+    build.build()
+    from paper_2606_15035_gb300 import sim as s
+    return s
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+def pdiff(x, y, L):
+    L = np.asarray(L)
+    d = np.asarray(x) - np.asarray(y)
+    return np.abs((d + 0.5 * L) % L - 0.5 * L).max()
+
+
+def pair(sim, x, v, q, m, n, L, dt=0.1, tol=1e-13, **kw):
+    okw = {k: kw[k] for k in ("quadrature", "nq", "split", "picard_max") if k in kw}
+    if "picard_accel" in kw:
+        okw["picard_accel"] = bool(kw["picard_accel"])
+    ckw = dict(kw)
+    if "split" in ckw:
+        ckw["split_orbit_at_knots"] = int(ckw.pop("split"))
+    if ckw.get("quadrature") == "gauss":
+        ckw["quadrature"] = 1
+    elif "quadrature" in ckw:
+        ckw["quadrature"] = 0
+    cfg = sim.pic_config_default(n=n, L=L, dt=dt, picard_tol=tol, **ckw)
+    ocfg = opic.Config(n=n, L=L, dt=dt, picard_tol=tol, **okw)
+    return sim.PicSim(cfg, x, v, q, m), ocfg
+
+
+def compare_state(st, o, ocfg, tol, L):
+    assert rel(st.v, o.v) <= tol, ("v", rel(st.v, o.v))
+    assert rel(st.P, o.P) <= tol, ("P", rel(st.P, o.P))
+    assert rel(st.vprev, o.vprev) <= tol
+    assert pdiff(st.x, opic.positions(o, ocfg), L) <= tol * max(L)
+    for name in ("phi", "psi", "rho", "A", "U"):
+        a, b = getattr(st, name), getattr(o, name)
+        scale = max(np.linalg.norm(b), 1e-14 * np.sqrt(b.size))
+        assert np.linalg.norm(a - b) / scale <= tol, (name, np.linalg.norm(a - b) / scale)
+
+
+def c1_inputs(per_beam=8, n=(8, 8, 8)):
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.random_twostream(n, w.L, per_beam, w.v0, w.eps, w.vth, w.seed)
+    return x, v, q, m, n, w.L
+
+
+def test_init_matches_oracle(sim):
+    x, v, q, m, n, L = c1_inputs()
+    s, ocfg = pair(sim, x, v, q, m, n, L)
+    st = s.get_state()
+    o = opic.init(x, v, q, m, ocfg)
+    assert rel(st.rho, o.rho) <= 1e-13
+    assert rel(st.phi, o.phi) <= 1e-13
+    assert np.abs(st.A).max() == 0.0 and np.abs(st.psi).max() == 0.0
+    np.testing.assert_array_equal(st.v, v)
+    assert rel(st.P, o.P) <= 1e-15
+    assert pdiff(st.x, x, L) <= 1e-15 * max(L)
+    s.close()
+
+
+def test_one_iteration_body_matches_oracle(sim):
+    x, v, q, m, n, L = c1_inputs()
+    s, ocfg = pair(sim, x, v, q, m, n, L)
+    o = opic.init(x, v, q, m, ocfg)
+    rng = np.random.default_rng(3)
+    v_it = v + 0.05 * rng.normal(size=v.shape)     # orbits crossing knots in every direction
+    g = s.iterate(v_it)
+    it = opic.picard_iteration(o, v_it, ocfg, ocfg.grid())
+    assert rel(g["J"], it["J"]) <= 1e-13
+    assert rel(g["rho"], it["rho"]) <= 1e-13
+    for name in ("phi", "psi", "A", "U"):
+        assert rel(g[name], it[name]) <= 1e-12, (name, rel(g[name], it[name]))
+    assert rel(g["P"], it["P"]) <= 1e-13
+    assert rel(g["v"], it["v_new"]) <= 1e-13
+    assert pdiff(g["x"], it["xi"] * np.asarray(ocfg.grid().H), L) <= 1e-14 * max(L)
+    s.close()
+
+
+@pytest.mark.parametrize("accel", [1, 0])
+def test_steps_and_diagnostics_match_oracle(sim, accel):
+    x, v, q, m, n, L = c1_inputs()
+    s, ocfg = pair(sim, x, v, q, m, n, L, tol=1e-14, diagnostics=1, picard_accel=accel)
+    o = opic.init(x, v, q, m, ocfg)
+    for _ in range(3):
+        info = s.step(1)
+        o, oinfo = opic.step(o, ocfg)
+        assert info.converged and oinfo["converged"]
+        assert abs(info.iterations - oinfo["iterations"]) <= 1
+        compare_state(s.get_state(), o, ocfg, 1e-12, L)
+        d = s.diagnostics()
+        E = d.K1 + d.W1
+        for a, b in [(d.K0, oinfo["K0"]), (d.W0, oinfo["W0"]), (d.K1, oinfo["K1"]), (d.W1, oinfo["W1"]),
+                     (d.particle_work, oinfo["particle_work"]), (d.mesh_work, oinfo["mesh_work"])]:
+            assert abs(a - b) <= 1e-12 * max(abs(b), 1e-6 * E), (a, b)
+        assert abs(d.R_total) <= 1e-14 * E and abs(d.R_field) <= 1e-14 * E and abs(d.R_particle) <= 1e-13 * E
+        assert d.RA_max <= 1e-15 and d.partition_max <= 1e-15
+        assert d.gauge_max <= 1e-12 and d.gauss_max <= 1e-11 and d.continuity_max <= 1e-13
+        assert abs(d.particle_work - d.mesh_work) <= 1e-13 * max(abs(d.mesh_work), 1e-6 * E)
+    s.close()
+
+
+def test_full_c1_run_matches_oracle_after_50_steps(sim):
+    """The 8^3 x 8192 cold two-stream workload, FP64, dt = 0.1, 50 steps, tau = 1e-14."""
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.workload_particles(w)
+    s, ocfg = pair(sim, x, v, q, m, w.n, w.L, dt=w.dt, tol=w.picard_tol)
+    o = opic.init(x, v, q, m, ocfg)
+    e0 = s.energy().total
+    drift = 0.0
+    for _ in range(w.steps):
+        info = s.step(1)
+        assert info.converged
+        drift = max(drift, abs(s.energy().total - e0) / e0)
+        o, oinfo = opic.step(o, ocfg)
+        assert oinfo["converged"]
+    compare_state(s.get_state(), o, ocfg, 1e-12, w.L)
+    assert drift <= 1e-12, drift
+    s.close()
+
+
+@pytest.mark.parametrize("split,nq", [(True, 3), (False, 16)])
+def test_gauss_quadrature_modes_match_oracle(sim, split, nq):
+    n, L = (6, 5, 4), (2 * np.pi / 3, 1.7, 1.3)
+    x, v, q, m = pi.random_twostream(n, L, 2, 0.2, 1e-3, 2e-2, 77)
+    s, ocfg = pair(sim, x, v, q, m, n, L, tol=1e-13, quadrature="gauss", nq=nq, split=split)
+    o = opic.init(x, v, q, m, ocfg)
+    for _ in range(2):
+        assert s.step(1).converged
+        o, oinfo = opic.step(o, ocfg)
+        assert oinfo["converged"]
+        compare_state(s.get_state(), o, ocfg, 1e-12, L)
+    s.close()
+
+
+def test_odd_grid_multi_knot_crossings_and_knot_starts(sim):
+    """Ragged grid (5, 6, 7), orbits crossing up to ~3 knots per step, starts on knots."""
+    n, L = (5, 6, 7), (0.25, 0.3, 0.35)
+    H = np.asarray(L) / np.asarray(n)
+    x, v, q, m = pi.random_twostream(n, L, 3, 0.6, 1e-2, 0.05, 91)
+    x[:40] = np.round(x[:40] / H) * H % np.asarray(L)     # some particles exactly on knots
+    s, ocfg = pair(sim, x, v, q, m, n, L, dt=0.2, tol=1e-13)
+    o = opic.init(x, v, q, m, ocfg)
+    beta = np.abs(0.2 * v / H).max()
+    assert beta > 2.0
+    for _ in range(2):
+        assert s.step(1).converged
+        o, oinfo = opic.step(o, ocfg)
+        assert oinfo["converged"]
+        compare_state(s.get_state(), o, ocfg, 1e-12, L)
+    s.close()
+
+
+def test_vacuum_fields_without_particles(sim):
+    n, L = (6, 4, 5), (1.0, 0.8, 0.9)
+    x = np.zeros((0, 3))
+    v = np.zeros((0, 3))
+    s, ocfg = pair(sim, x, v, -1.0, 1.0, n, L, tol=1e-13)
+    rng = np.random.default_rng(5)
+    st = s.get_state()
+    st.phi = rng.normal(size=n)
+    st.psi = rng.normal(size=n)
+    st.A = rng.normal(size=(3,) + n)
+    st.U = rng.normal(size=(3,) + n)
+    st.rho = rng.normal(size=n)
+    s.set_state(st)
+    o = opic.State(xi=np.zeros((0, 3)), v=v, P=v.copy(), vprev=v.copy(), q=-1.0, m=1.0, phi=st.phi, psi=st.psi,
+                   A=st.A, U=st.U, rho=st.rho)
+    for _ in range(3):
+        assert s.step(1).converged
+        o, oinfo = opic.step(o, ocfg)
+        assert oinfo["converged"]
+    g = s.get_state()
+    for name in ("phi", "psi", "A", "U", "rho"):
+        assert rel(getattr(g, name), getattr(o, name)) <= 1e-12, name
+    s.close()
+
+
+def test_nonconvergence_keeps_committed_state(sim):
+    from paper_2606_15035_gb300._lib import PicError
+    x, v, q, m, n, L = c1_inputs(per_beam=2)
+    s, _ = pair(sim, x, v, q, m, n, L, tol=1e-14, picard_max=0)
+    before = s.get_state()
+    with pytest.raises(PicError) as e:
+        s.step(1)
+    assert e.value.status == 4
+    after = s.get_state()
+    for name in ("x", "v", "P", "vprev", "phi", "psi", "rho", "A", "U"):
+        np.testing.assert_array_equal(getattr(after, name), getattr(before, name))
+    s.close()
+
+
+def test_checkpoint_restart_roundtrip(sim):
+    x, v, q, m, n, L = c1_inputs(per_beam=4)
+    a, _ = pair(sim, x, v, q, m, n, L)
+    a.step(2)
+    ck = a.get_state()
+    b, _ = pair(sim, x, v, q, m, n, L)
+    b.set_state(ck)
+    a.step(1)
+    b.step(1)
+    sa, sb = a.get_state(), b.get_state()
+    for name in ("v", "P", "phi", "A", "rho"):
+        assert rel(getattr(sb, name), getattr(sa, name)) <= 1e-13, name
+    a.close()
+    b.close()
+
+
+def test_invalid_configurations_are_rejected(sim):
+    from paper_2606_15035_gb300._lib import PicError
+    x, v, q, m, n, L = c1_inputs(per_beam=1)
+    for bad in [dict(split_orbit_at_knots=0), dict(nq=0, quadrature=1), dict(dt=-1.0)]:
+        cfg = sim.pic_config_default(n=n, L=L, **bad)
+        with pytest.raises(PicError) as e:
+            sim.PicSim(cfg, x, v, q, m)
+        assert e.value.status == 1
+
+
+def test_full_size_32c_workload(sim):
+    """32^3 grid, 2,097,152 particles (the benchmark workload), FP64 launch configuration."""
+    w = pi.WORKLOADS["twostream-32c-2M"]
+    x, v, q, m = pi.workload_particles(w)
+    s, ocfg = pair(sim, x, v, q, m, w.n, w.L, dt=w.dt, tol=w.picard_tol, diagnostics=1)
+    grid = ocfg.grid()
+    o = opic.init(x, v, q, m, ocfg)
+    st = s.get_state()
+    assert rel(st.rho, o.rho) <= 1e-13 and rel(st.phi, o.phi) <= 1e-13
+    # one Algorithm 1 body at full size: current and mesh update in full
+    g = s.iterate(v)
+    J = np.zeros((3,) + grid.n)
+    H = np.asarray(grid.H)
+    beta = w.dt * v / H
+    for sl in opic._chunks(x.shape[0]):
+        ow = opic.orbit_weights(o.xi[sl], beta[sl], ocfg, grid, with_gradient=False)
+        J += opic.orbit.deposit(q * v[sl], ow, grid)
+    assert rel(g["J"], J) <= 1e-12
+    rho1 = omesh.continuity(o.rho, J, w.dt, grid)
+    phi1, psi1, A1, U1 = omesh.cn_fields(o.phi, o.psi, o.A, o.U, 0.5 * (rho1 + o.rho), J, w.dt, 1.0, 1.0, 1.0, grid)
+    for name, ref in [("rho", rho1), ("phi", phi1), ("psi", psi1), ("A", A1), ("U", U1)]:
+        assert rel(g[name], ref) <= 1e-12, name
+    # the push on a sample of particles, with the oracle's own fields
+    idx = np.random.default_rng(0).choice(x.shape[0], 4096, replace=False)
+    gphi = omesh.grad(0.5 * (phi1 + o.phi), grid)
+    pushed = opic.push_particles(o.xi[idx], v[idx], o.P[idx], v[idx], q, m, o.A, A1, gphi, 0.5 * (U1 + o.U),
+                                 ocfg, grid)
+    assert rel(g["P"][idx], pushed["P"]) <= 1e-12
+    assert rel(g["v"][idx], pushed["v_new"]) <= 1e-12
+    assert pdiff(g["x"][idx], pushed["xi"] * H, w.L) <= 1e-13 * max(w.L)
+    # two committed steps: the paper's identities at full size
+    e0 = s.energy().total
+    for _ in range(2):
+        info = s.step(1)
+        assert info.converged
+        d = s.diagnostics()
+        E = d.K1 + d.W1
+        assert abs(d.R_total) <= 1e-13 * E and d.RA_max <= 1e-14 and d.partition_max <= 1e-14
+        assert d.gauge_max <= 1e-11 and d.continuity_max <= 1e-12
+    assert abs(s.energy().total - e0) <= 1e-13 * e0
+    s.close()
+
+
+def _strong_A_state(sim_mod, accel):
+    """Random particles with a smooth divergence-free A^n: creeping knot crossings make the
+    plain Picard map non-contractive; the particle-local solves restore convergence."""
+    from oracle import mesh, orbit
+    x, v, q, m, n, L = c1_inputs(per_beam=4)
+    ocfg = opic.Config(n=n, L=L, dt=0.1, picard_tol=1e-13, picard_max=30, picard_accel=bool(accel))
+    o = opic.init(x, v, q, m, ocfg)
+    grid = ocfg.grid()
+    rng = np.random.default_rng(21)
+    F = np.stack([mesh.project_out_null(rng.normal(size=grid.n), grid) for _ in range(3)])
+    for _ in range(2):
+        F = F + 0.25 * np.stack([mesh.lap(F[c], grid) * min(grid.H) ** 2 for c in range(3)])
+    A = mesh.curl(F, grid)
+    A *= 0.05 / np.abs(A).max()
+    o = opic.replace(o, A=A)
+    o = opic.replace(o, P=o.m * o.v + o.q * orbit.point_gather(A, o.xi, grid).T)
+    cfg = sim_mod.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-13, picard_max=30, picard_accel=accel)
+    s = sim_mod.PicSim(cfg, x, v, q, m)
+    st = s.get_state()
+    st.x, st.v, st.P, st.vprev = opic.positions(o, ocfg), o.v, o.P, o.vprev
+    st.phi, st.psi, st.A, st.U, st.rho = o.phi, o.psi, o.A, o.U, o.rho
+    s.set_state(st)
+    return s, o, ocfg, L
+
+
+def test_local_solves_match_oracle_where_plain_picard_cycles(sim):
+    from paper_2606_15035_gb300._lib import PicError
+    s, o, ocfg, L = _strong_A_state(sim, 0)
+    with pytest.raises(PicError) as e:
+        s.step(1)
+    assert e.value.status == 4
+    s.close()
+    s, o, ocfg, L = _strong_A_state(sim, 1)
+    info = s.step(1)
+    o1, oinfo = opic.step(o, ocfg)
+    assert info.converged and oinfo["converged"]
+    compare_state(s.get_state(), o1, ocfg, 1e-12, L)
+    s.close()
