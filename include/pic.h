@@ -196,6 +196,15 @@ pic_status pic_set_state(pic_ctx* ctx, const pic_state_view* src);
  * out the orbit current, the new mesh fields and the pushed particles. */
 pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, const pic_iterate_out* out);
 
+/* Particle positions exactly as stored, in cell units xi = x / H (3 * np, pic_init order,
+ * wrapped to [0, n_a)): the orbit breakpoints and knot tests of §4.7 use these values. */
+pic_status pic_get_positions(pic_ctx* ctx, double* xi, int32_t on_device);
+
+/* After a pic_step that did not converge: its last Picard iterate v^{n+1,p} and the image
+ * G(v^{n+1,p}) (3 * np each, particles in pic_init order); their difference is each
+ * particle's fixed-point residual (Algorithm 1).  PIC_ERR_ARG after a converged step. */
+pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t on_device);
+
 /* Switch live profiling on (1) or off (0).  If `out` is non-NULL the accumulated profile is
  * copied there (after synchronising the stream) and the accumulators are reset. */
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);

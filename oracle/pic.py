@@ -8,7 +8,8 @@ Readings of points the paper leaves open (each is listed in the design notes):
 
 * History velocity at the first step: v^{-1} := v^0, so the first guess is v^0.
 * Picard norms: e_v = ||v^{n+1,p+1} - v^{n+1,p}||_2 / ||v^{n+1,p+1}||_2 over all
-  particles and components; e_J = ||J^p - J^{p-1}||_2 / (||J^p||_2 + J_scale) with
+  particles and components, v^{n+1,p+1} being the next iterate (G(v^{n+1,p}) itself for
+  plain Picard); e_J = ||J^p - J^{p-1}||_2 / (||J^p||_2 + J_scale) with
   J_scale = sqrt(N_cells) * sum_i |q_i| |v_i^n| / |Omega| (a floor, because the
   paired beams start with J ~ 0, §5.4); e_J is not defined at p = 0, so p = 0
   never converges.  Converged when both are <= tau.
@@ -22,10 +23,18 @@ Readings of points the paper leaves open (each is listed in the design notes):
   knot on an axis where it moves very little (|beta_a| < 0.1 cells, "creeping") has a
   step force that is very sensitive to its own velocity: the orbit average of d_j S in
   D_i A changes with the fraction of the path beyond the knot.  The particle-local
-  feedback can exceed 1, and plain Picard then stalls or cycles on it.  With
+  feedback can exceed 1, and plain Picard then stalls or cycles on it (also when an
+  iterate flips between crossing and just missing the knot).  With
   ``picard_accel`` each iteration therefore solves, for the creeping particles only, the
-  particle's own equation v = G_i(v) with the iteration's fields held fixed (secant steps
-  per component, at most LOCAL_STEPS evaluations, keeping the best iterate); every other
+  particle's own equation v = G_i(v) with the iteration's fields held fixed (per component:
+  secant steps while they converge, else growing steps along g until the root is bracketed,
+  then Illinois steps; at most LOCAL_STEPS evaluations; the best iterate is kept).  A
+  particle that barely crosses a knot can have no root near its iterate (the two sides of
+  the crossing threshold push the same way); g = G - u is continuous and G bounded, so a
+  root lies in the direction of g.  A particle that starts exactly on a knot can have no
+  root at all (G jumps where its orbit lands on the knot, both sides pushing onto it); it
+  then lands exactly on the knot and slides along it (Filippov solution; see local_solve),
+  which keeps the energy identities exact.  Every other
   particle takes Algorithm 1's update v^{p+1} = G(v^p).  The outer loop then contracts at
   the rate of the weak particle-field coupling.  With ``picard_accel=False`` every particle
   takes the plain update.
@@ -44,7 +53,9 @@ from . import mesh, orbit
 
 CHUNK = 32768
 BETA_CREEP = 0.1      # cells: "creeping" knot crossings get a particle-local solve
-LOCAL_STEPS = 8       # at most this many extra push evaluations per creeping particle
+D_KNOT = 1e-6         # cells: starting this close to a knot also counts as creeping
+SLIDE_PROBE = 1e-12   # cells: the sliding test probes beta = d -+ SLIDE_PROBE
+LOCAL_STEPS = 24      # at most this many extra push evaluations per creeping particle
 LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
 OMEGA_MAX = 8.0       # bound on the secant step factor
 
@@ -136,7 +147,7 @@ def init(x, v, q, m, cfg):
 
 # --- Algorithm 1 ---------------------------------------------------------------------
 
-def picard_iteration(st, v_it, cfg, grid, diagnostics=False):
+def picard_iteration(st, v_it, cfg, grid, diagnostics=False, slide=None):
     """One pass of the Algorithm 1 loop body for the end-of-step velocity iterate ``v_it``."""
     H = np.asarray(grid.H)
     dt = cfg.dt
@@ -156,7 +167,7 @@ def picard_iteration(st, v_it, cfg, grid, diagnostics=False):
     gphi_half = mesh.grad(0.5 * (phi1 + st.phi), grid)
     U_half = 0.5 * (U1 + st.U)
     pushed = push_particles(st.xi, st.v, st.P, v_it, st.q, st.m, st.A, A1, gphi_half, U_half, cfg, grid,
-                            diagnostics)
+                            diagnostics, slide)
     P1, xi1, v_new = pushed["P"], pushed["xi"], pushed["v_new"]
     diag = pushed.get("diag")
     out = dict(J=J, rho=rho1, phi=phi1, psi=psi1, A=A1, U=U1, P=P1, xi=xi1, v_new=v_new, vbar=vbar,
@@ -168,11 +179,13 @@ def picard_iteration(st, v_it, cfg, grid, diagnostics=False):
     return out
 
 
-def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, diagnostics=False):
+def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, diagnostics=False, slide=None):
     """Orbit gather and canonical-momentum push of Algorithm 1 for the given particles.
 
     Uses the midpoint mesh fields of the current iterate: grad_h phi^{n+1/2} (3, n...),
     A^n and A^{n+1} for the orbit-discrete gradient, and U^{n+1/2} (diagnostics only).
+    ``slide`` (np, 3) marks components sliding onto a knot (see local_solve): there the
+    orbit lands on the knot, v^{n+1}_a is the iterate itself and P_a = m v_a + q A_h,a(x^{n+1}).
     """
     H = np.asarray(grid.H)
     dt = cfg.dt
@@ -193,6 +206,10 @@ def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, d
         xi1[sl] = wrap_cells(xend, grid.n)
         A_end = orbit.point_gather(A1, xi1[sl], grid).T              # A_h^{n+1}(x^{n+1})
         v_new[sl] = (P1[sl] - q * A_end) / m                         # Eq. (orbit-v-update)
+        if slide is not None:
+            sv = slide[sl]
+            v_new[sl] = np.where(sv, v_it[sl], v_new[sl])
+            P1[sl] = np.where(sv, m * v_new[sl] + q * A_end, P1[sl])
         if diagnostics:
             Ubar = orbit.gather(U_half, ow).T                        # Eq. (Ubar-def)
             A_start = orbit.point_gather(A0, xi[sl], grid).T
@@ -208,49 +225,117 @@ def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, d
 
 
 def creeping(xi, beta):
-    """Particles whose orbit crosses a knot on an axis with 0 < |beta_a| < BETA_CREEP (cells)."""
+    """Particles that, on an axis with |beta_a| < BETA_CREEP (cells), get within 2 |beta_a| of
+    the next knot ahead (d in (0, 1]) or start within D_KNOT of any knot: the orbits that
+    cross a knot while barely moving, those that nearly do, and those hovering on a knot (an
+    iterate can flip between crossing and not crossing)."""
     f = np.zeros(xi.shape[0], dtype=bool)
     for a in range(3):
-        b = beta[:, a]
-        f |= (np.floor(xi[:, a] + b) != np.floor(xi[:, a])) & (np.abs(b) < BETA_CREEP) & (b != 0)
+        x, b = xi[:, a], beta[:, a]
+        d = np.where(b > 0, np.floor(x) + 1.0 - x, x - (np.ceil(x) - 1.0))
+        near = np.minimum(x - np.floor(x), np.ceil(x) - x)
+        f |= (np.abs(b) < BETA_CREEP) & (((b != 0) & (d < 2.0 * np.abs(b))) | (near < D_KNOT))
     return f
 
 
-def local_solve(st, v_it, it, cfg, grid):
-    """Next iterate: G(v^p) for most particles; for the creeping ones the root of
-    v = G_i(v) with this iteration's fields fixed (secant per component, best iterate kept)."""
+def local_solve(st, v_it, it, cfg, grid, pinned=None):
+    """Next iterate: G(v^p) for most particles; for the creeping ones a root of
+    g(u) = G_i(u) - u with this iteration's fields fixed, per component.
+
+    * Sliding.  For a component starting within D_KNOT of a knot, g is probed just short of
+      and just past landing on that knot (beta_a = d -+ SLIDE_PROBE, d the signed distance).
+      If both sides push onto the knot there is no root: the orbit average of d_a S, and so
+      G, jumps there.  The component then lands exactly on the knot (beta_a = d, the
+      Filippov sliding solution) and the push completes it with v^{n+1}_a = u_a and P_a from
+      the canonical relation.  Energy is unaffected: the a-component work and the a-column
+      of D_i A are multiplied by vbar_a = d H_a / dt, which is below D_KNOT H_a / dt.
+    * Otherwise: secant steps (factor clamped to [-OMEGA_MAX, OMEGA_MAX]) while each one at
+      least halves |g|, so a nearby root is found first; else steps u + f g along g with
+      f = 2, 4, 8, ... (g is continuous there and G bounded, so g changes sign that way);
+      inside a bracket, Illinois (modified regula falsi) steps.  At most LOCAL_STEPS
+      evaluations; each component's best iterate is kept.
+
+    ``pinned`` (np, 3): components found sliding earlier in this step; they stay pinned, so
+    that the outer iteration cannot cycle between pinned and free.
+    Returns (v_next, slide mask)."""
     H = np.asarray(grid.H)
     G = it["v_new"]
     v_next = G.copy()
+    slide = np.zeros(G.shape, dtype=bool)
     beta = cfg.dt * 0.5 * (v_it + st.v) / H
     idx = np.nonzero(creeping(st.xi, beta))[0]
     if idx.size == 0:
-        return v_next
+        return v_next, slide
 
     def Gf(u):
         return push_particles(st.xi[idx], st.v[idx], st.P[idx], u, st.q, st.m, st.A, it["A"], it["gphi_half"],
                               it["U_half"], cfg, grid)["v_new"]
 
+    x0 = st.xi[idx]
+    vn = st.v[idx]
     u0, r0 = v_it[idx], G[idx] - v_it[idx]
     u1 = G[idx]
+    # sliding probes, one axis at a time on the base vector u1
+    d_knot = np.round(x0) - x0
+    near = np.abs(d_knot) < D_KNOT
+    u_land = 2.0 * d_knot * H / cfg.dt - vn
+    sl = np.zeros(u1.shape, dtype=bool) if pinned is None else pinned[idx].copy()
+    for a in range(3):
+        cand = near[:, a] & ~sl[:, a]
+        if not np.any(cand):
+            continue
+        um, up = u1.copy(), u1.copy()
+        um[:, a] = 2.0 * (d_knot[:, a] - SLIDE_PROBE) * H[a] / cfg.dt - vn[:, a]
+        up[:, a] = 2.0 * (d_knot[:, a] + SLIDE_PROBE) * H[a] / cfg.dt - vn[:, a]
+        gm = Gf(um)[:, a] - um[:, a]
+        gp = Gf(up)[:, a] - up[:, a]
+        sl[:, a] |= cand & (gm > 0) & (gp < 0)
+    u1 = np.where(sl, u_land, u1)
     r1 = Gf(u1) - u1
-    scale = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)[:, None]
-    best_u = np.where(np.abs(r1) < np.abs(r0), u1, u0)
-    best_r = np.minimum(np.abs(r1), np.abs(r0))
+    r0 = np.where(sl, 0.0, r0)
+    r1 = np.where(sl, 0.0, r1)
+    tol = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)[:, None]
+    best_u = np.where(sl | (np.abs(r1) < np.abs(r0)), u1, u0)
+    best_r = np.where(sl, 0.0, np.minimum(np.abs(r1), np.abs(r0)))
+    br = ~sl & (r0 * r1 < 0)                          # bracketed components
+    ua, ga, ub, gb = u0.copy(), r0.copy(), u1.copy(), r1.copy()
+    side = np.zeros_like(u0)
+    secant_ok = np.abs(r1) <= 0.5 * np.abs(r0)        # the plain step at least halved |g|
+    fac = np.full_like(u0, 2.0)
     for _ in range(LOCAL_STEPS - 1):
-        if np.all(best_r <= scale):
+        if np.all(best_r <= tol):
             break
         with np.errstate(divide="ignore", invalid="ignore"):
             sec = -(u1 - u0) / (r1 - r0)
+            fp = ub - gb * (ub - ua) / (gb - ga)
         sec = np.where(np.isfinite(sec), np.clip(sec, -OMEGA_MAX, OMEGA_MAX), 1.0)
-        u2 = u1 + sec * r1
-        r2 = Gf(u2) - u2
-        better = np.abs(r2) < best_r
+        expand = ~br & ~secant_ok
+        u2 = np.where(br & np.isfinite(fp), fp, np.where(expand, u1 + fac * r1, u1 + sec * r1))
+        u2 = np.where(sl, u_land, u2)
+        fac = np.where(expand, 2.0 * fac, fac)
+        r2 = np.where(sl, 0.0, Gf(u2) - u2)
+        better = ~sl & (np.abs(r2) < best_r)
         best_u = np.where(better, u2, best_u)
         best_r = np.where(better, np.abs(r2), best_r)
+        secant_ok = secant_ok & (np.abs(r2) <= 0.5 * np.abs(r1))
+        # bracket bookkeeping (Illinois: halve the kept end's value when it is kept twice)
+        same_b = br & (r2 * gb > 0)
+        same_a = br & ~same_b
+        ga = np.where(same_b & (side > 0), 0.5 * ga, ga)
+        gb = np.where(same_a & (side < 0), 0.5 * gb, gb)
+        ub, gb = np.where(same_b, u2, ub), np.where(same_b, r2, gb)
+        ua, ga = np.where(same_a, u2, ua), np.where(same_a, r2, ga)
+        side = np.where(same_b, 1.0, np.where(same_a, -1.0, side))
+        new_br = ~sl & ~br & (r2 * r1 < 0)
+        ua, ga = np.where(new_br, u1, ua), np.where(new_br, r1, ga)
+        ub, gb = np.where(new_br, u2, ub), np.where(new_br, r2, gb)
+        br = br | new_br
         u0, r0, u1, r1 = u1, r1, u2, r2
     v_next[idx] = best_u
-    return v_next
+    if pinned is not None:
+        slide |= pinned
+    slide[idx] = sl
+    return v_next, slide
 
 
 def j_scale(st, grid):
@@ -269,10 +354,15 @@ def step(st, cfg):
     jsc = j_scale(st, grid)
     hist = []
     converged = False
+    slide = None
     for p in range(cfg.picard_max + 1):
         it = picard_iteration(st, v_it, cfg, grid)
-        vnorm = np.linalg.norm(it["v_new"])
-        e_v = np.linalg.norm(it["v_new"] - v_it) / vnorm if vnorm > 0 else 0.0   # no particles: no error
+        if cfg.picard_accel:
+            v_next, slide = local_solve(st, v_it, it, cfg, grid, slide)
+        else:
+            v_next, slide = it["v_new"], None
+        vnorm = np.linalg.norm(v_next)
+        e_v = np.linalg.norm(v_next - v_it) / vnorm if vnorm > 0 else 0.0   # no particles: no error
         if J_prev is None:
             e_J = np.inf
         else:
@@ -282,13 +372,12 @@ def step(st, cfg):
         if e_v <= cfg.picard_tol and e_J <= cfg.picard_tol:
             converged = True
             break
-        v_it = local_solve(st, v_it, it, cfg, grid) if cfg.picard_accel else it["v_new"]
+        v_it = v_next
         J_prev = it["J"]
     info = {"converged": converged, "iterations": len(hist), "errors": hist}
     if not converged:
         return st, info
-    v_fin = local_solve(st, v_it, it, cfg, grid) if cfg.picard_accel else it["v_new"]
-    fin = picard_iteration(st, v_fin, cfg, grid, diagnostics=True)
+    fin = picard_iteration(st, v_next, cfg, grid, diagnostics=True, slide=slide)
     new = State(xi=fin["xi"], v=fin["v_new"], P=fin["P"], vprev=st.v.copy(), q=st.q, m=st.m,
                 phi=fin["phi"], psi=fin["psi"], A=fin["A"], U=fin["U"], rho=fin["rho"])
     K0, W0 = energy(st, cfg)

@@ -306,16 +306,25 @@ __global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, con
 
 // Constants of the particle-local solve for "creeping" particles (see k_local).
 constexpr double BETA_CREEP = 0.1;   // cells
-constexpr int LOCAL_STEPS = 8;       // push evaluations per creeping particle
+constexpr int LOCAL_STEPS = 24;      // push evaluations per creeping particle
 constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
 constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
+constexpr double D_KNOT = 1e-6;      // cells: starting this close to a knot also counts
+constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes beta = d -+ SLIDE_PROBE
 
-// Does the orbit cross a knot on an axis where it moves less than BETA_CREEP cells?
+// On an axis where the orbit moves less than BETA_CREEP cells, does it get within 2 |beta|
+// of the next knot ahead, or start within D_KNOT of any knot?  Those orbits cross a knot
+// while barely moving, nearly do, or hover on a knot (an iterate can flip between
+// crossing and not crossing).
 __device__ __forceinline__ bool is_creeping(const double x0[3], const double beta[3]) {
     bool f = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        f |= (beta[a] != 0.0) && (fabs(beta[a]) < BETA_CREEP) && (floor(x0[a] + beta[a]) != floor(x0[a]));
+    for (int a = 0; a < 3; ++a) {
+        const double b = beta[a];
+        const double d = b > 0.0 ? floor(x0[a]) + 1.0 - x0[a] : x0[a] - (ceil(x0[a]) - 1.0);
+        const double near = fmin(x0[a] - floor(x0[a]), ceil(x0[a]) - x0[a]);
+        f |= (fabs(b) < BETA_CREEP) && (((b != 0.0) && (d < 2.0 * fabs(b))) || (near < D_KNOT));
+    }
     return f;
 }
 
@@ -368,7 +377,8 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
                                                   double* __restrict__ vnew, double* __restrict__ Jnext,
                                                   double* __restrict__ xi_out, double* __restrict__ P_out,
                                                   int32_t* __restrict__ creep_list, int* __restrict__ creep_count,
-                                                  double* __restrict__ partials, int* __restrict__ status) {
+                                                  const uint8_t* __restrict__ slide, double* __restrict__ partials,
+                                                  int* __restrict__ status) {
     __shared__ double sm[32];
     const int64_t np = p.np;
     double ev_num = 0.0, ev_den = 0.0, pieces_push = 0.0, pieces_scatter = 0.0;
@@ -391,28 +401,38 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
 #pragma unroll
         for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
         if constexpr (!COMMIT) {
-            double beta_it[3], wv[3], bet2[3];
+            double beta_it[3], wv[3], bet2[3], dnum = 0.0, dden = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double d = o.vw[a] - vi[a];   // Picard residual r = G(v) - v
-                ev_num += d * d;
-                ev_den += o.vw[a] * o.vw[a];
+                double d = o.vw[a] - vi[a];   // change of the iterate, v^{p+1} - v^p
+                dnum += d * d;
+                dden += o.vw[a] * o.vw[a];
                 beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
                 double vb2 = 0.5 * (o.vw[a] + vn[a]);
                 bet2[a] = p.dt * vb2 * p.invH[a];
                 wv[a] = p.q_dV * vb2;
             }
             if (p.accel && is_creeping(x0, beta_it)) {
-                int k = atomicAdd(creep_count, 1);
+                int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
                 creep_list[k] = (int32_t)i;
             } else {
+                ev_num += dnum;
+                ev_den += dden;
                 int ns = scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext);
                 if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
                 pieces_scatter += (double)ns;
             }
         } else {
+            // components sliding onto a knot (set by k_local): the orbit lands on the knot,
+            // v^{n+1}_a is the iterate itself and P_a follows from v = (P - q A_h(x)) / m
+            const uint8_t sb = slide ? slide[i] : 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
+                if (sb & (1u << a)) {
+                    o.vw[a] = vi[a];
+                    o.Pw[a] = p.mass * o.vw[a] + p.q * o.Ae[a];
+                    vnew[a * np + i] = o.vw[a];
+                }
                 xi_out[a * np + i] = o.xe[a];
                 P_out[a * np + i] = o.Pw[a];
             }
@@ -449,22 +469,38 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
 }
 
 // Particle-local solve of v = G_i(v) with the iteration's fields fixed, for the creeping
-// particles listed by k_push (§4.8 allows any converged solver).  Secant steps per
-// component from the pair (v^p, G(v^p)), (G(v^p), G(G(v^p))), ...: at most LOCAL_STEPS
-// push evaluations, stopping when every component's residual is below LOCAL_TOL times the
-// particle's speed; the best iterate per component is kept.  Then its orbit current.
+// particles listed by k_push (§4.8 allows any converged solver).  Per component of
+// g(u) = G_i(u) - u, starting from (v^p, G(v^p)): clamped secant steps while each one at
+// least halves |g| (a nearby root is found first); otherwise steps u + f g with f = 2, 4,
+// 8, ... (g is continuous and G bounded, so g changes sign that way: a particle that barely
+// crosses a knot can have no root near its iterate); inside a bracket, Illinois (modified
+// regula falsi) steps.  At most LOCAL_STEPS push evaluations, stopping when every
+// component's residual is below LOCAL_TOL times the particle's speed; each component's best
+// iterate is kept.  Sliding (sticky for the rest of the step once detected, so that the
+// outer iteration cannot cycle between pinned and free): a component starting within D_KNOT
+// of a knot whose two sides
+// (beta_a = d -+ SLIDE_PROBE, d the signed distance) both push onto the knot has no root (G
+// jumps there); it lands exactly on the knot (the Filippov solution) and the commit push sets
+// v^{n+1}_a to it with P_a from the canonical relation; vbar_a = d H / dt < D_KNOT H / dt, so
+// the energy identities are unaffected.  The plain image G(v^p) is saved in gsave
+// (diagnostics), then the orbit current of the result is scattered.
 template <int QUAD>
 __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* __restrict__ xi,
                                                    const double* __restrict__ v, const double* __restrict__ P,
                                                    const double* __restrict__ vit, const double* __restrict__ table,
-                                                   double* __restrict__ vnew, double* __restrict__ Jnext,
-                                                   const int32_t* __restrict__ creep_list,
-                                                   const int* __restrict__ creep_count, int* __restrict__ status) {
+                                                   double* __restrict__ vnew, double* __restrict__ gsave,
+                                                   double* __restrict__ Jnext, const int32_t* __restrict__ creep_list,
+                                                   const int* __restrict__ creep_count, uint8_t* __restrict__ slide,
+                                                   double* __restrict__ partials, int* __restrict__ status) {
+    __shared__ double sm[32];
     const int64_t np = p.np;
     const int count = *creep_count;
+    double ev_num = 0.0, ev_den = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
         const int64_t i = creep_list[k];
         double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
+        double ua[3], ga[3], ub[3], gb[3], side[3], fac[3];
+        bool brk[3], secok[3];
         double nrm = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -473,38 +509,103 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
             Pn[a] = P[a * np + i];
             u0[a] = vit[a * np + i];
             u1[a] = vnew[a * np + i];          // G(v^p) from k_push
+            gsave[a * np + i] = u1[a];
             r0[a] = u1[a] - u0[a];
             nrm += u0[a] * u0[a];
         }
         const double tol = LOCAL_TOL * fmax(sqrt(nrm), 1e-300);
         PushAcc acc;
         PushOut o;
+        // Sliding probes: a component starting within D_KNOT of a knot is tested just short of
+        // and just past landing on it (beta_a = d -+ SLIDE_PROBE); if both sides push onto the
+        // knot there is no root (G jumps there) and the component lands exactly on the knot.
+        bool sl[3] = {false, false, false};
+        double uland[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double dk = rint(x0[a]) - x0[a];
+            uland[a] = 2.0 * dk * p.H[a] / p.dt - vn[a];
+            if ((slide[i] >> a) & 1u) {
+                sl[a] = true;                            // pinned earlier in this step: stays pinned
+            } else if (fabs(dk) < D_KNOT) {
+                double um[3] = {u1[0], u1[1], u1[2]}, up[3] = {u1[0], u1[1], u1[2]};
+                um[a] = 2.0 * (dk - SLIDE_PROBE) * p.H[a] / p.dt - vn[a];
+                up[a] = 2.0 * (dk + SLIDE_PROBE) * p.H[a] / p.dt - vn[a];
+                push_eval<QUAD, false>(p, x0, vn, Pn, um, table, acc, o);
+                const double gm = o.vw[a] - um[a];
+                push_eval<QUAD, false>(p, x0, vn, Pn, up, table, acc, o);
+                const double gp = o.vw[a] - up[a];
+                sl[a] = gm > 0.0 && gp < 0.0;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (sl[a]) u1[a] = uland[a];
         push_eval<QUAD, false>(p, x0, vn, Pn, u1, table, acc, o);
         if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            r1[a] = o.vw[a] - u1[a];
-            bool b1 = fabs(r1[a]) < fabs(r0[a]);
+            r1[a] = sl[a] ? 0.0 : o.vw[a] - u1[a];
+            if (sl[a]) r0[a] = 0.0;
+            const bool b1 = sl[a] || fabs(r1[a]) < fabs(r0[a]);
             bu[a] = b1 ? u1[a] : u0[a];
-            br[a] = b1 ? fabs(r1[a]) : fabs(r0[a]);
+            br[a] = sl[a] ? 0.0 : (b1 ? fabs(r1[a]) : fabs(r0[a]));
+            brk[a] = !sl[a] && r0[a] * r1[a] < 0.0;
+            ua[a] = u0[a];
+            ga[a] = r0[a];
+            ub[a] = u1[a];
+            gb[a] = r1[a];
+            side[a] = 0.0;
+            secok[a] = fabs(r1[a]) <= 0.5 * fabs(r0[a]);
+            fac[a] = 2.0;
         }
         for (int step = 0; step < LOCAL_STEPS - 1; ++step) {
             if (br[0] <= tol && br[1] <= tol && br[2] <= tol) break;
             double u2[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
+                const double fp = ub[a] - gb[a] * (ub[a] - ua[a]) / (gb[a] - ga[a]);
                 double sec = -(u1[a] - u0[a]) / (r1[a] - r0[a]);
                 sec = isfinite(sec) ? fmin(fmax(sec, -OMEGA_MAX), OMEGA_MAX) : 1.0;
-                u2[a] = u1[a] + sec * r1[a];
+                if (sl[a]) {
+                    u2[a] = uland[a];                    // pinned: lands on the knot
+                } else if (brk[a] && isfinite(fp)) {
+                    u2[a] = fp;                          // Illinois inside the bracket
+                } else if (!brk[a] && !secok[a]) {
+                    u2[a] = u1[a] + fac[a] * r1[a];      // grow along g until g changes sign
+                    fac[a] *= 2.0;
+                } else {
+                    u2[a] = u1[a] + sec * r1[a];         // secant while it converges
+                }
             }
             push_eval<QUAD, false>(p, x0, vn, Pn, u2, table, acc, o);
             if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double r2 = o.vw[a] - u2[a];
-                if (fabs(r2) < br[a]) {
+                const double r2 = sl[a] ? 0.0 : o.vw[a] - u2[a];
+                if (!sl[a] && fabs(r2) < br[a]) {
                     br[a] = fabs(r2);
                     bu[a] = u2[a];
+                }
+                secok[a] = secok[a] && fabs(r2) <= 0.5 * fabs(r1[a]);
+                if (brk[a]) {
+                    if (r2 * gb[a] > 0.0) {            // replaces the b end
+                        if (side[a] > 0.0) ga[a] *= 0.5;
+                        ub[a] = u2[a];
+                        gb[a] = r2;
+                        side[a] = 1.0;
+                    } else {                           // replaces the a end
+                        if (side[a] < 0.0) gb[a] *= 0.5;
+                        ua[a] = u2[a];
+                        ga[a] = r2;
+                        side[a] = -1.0;
+                    }
+                } else if (!sl[a] && r2 * r1[a] < 0.0) {
+                    brk[a] = true;
+                    ua[a] = u1[a];
+                    ga[a] = r1[a];
+                    ub[a] = u2[a];
+                    gb[a] = r2;
                 }
                 u0[a] = u1[a];
                 r0[a] = r1[a];
@@ -512,17 +613,30 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                 r1[a] = r2;
             }
         }
+        uint8_t sb = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (sl[a]) {
+                bu[a] = uland[a];
+                sb |= (uint8_t)(1u << a);
+            }
+        slide[i] = sb;
         double wv[3], bet2[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (!isfinite(bu[a])) atomicOr(status, DEV_ERR_NONFINITE);
+            const double d = bu[a] - vit[a * np + i];
+            ev_num += d * d;
+            ev_den += bu[a] * bu[a];
             vnew[a * np + i] = bu[a];
-            double vb2 = 0.5 * (bu[a] + vn[a]);
+            const double vb2 = 0.5 * (bu[a] + vn[a]);
             bet2[a] = p.dt * vb2 * p.invH[a];
             wv[a] = p.q_dV * vb2;
         }
         if (scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
     }
+    write_partial<double>(partials, S_EVL_NUM, ev_num, sm, false);
+    write_partial<double>(partials, S_EVL_DEN, ev_den, sm, false);
 }
 
 __global__ void k_kinetic(StepParams p, const double* __restrict__ v, double* __restrict__ partials) {
@@ -661,6 +775,8 @@ StepParams make_params(const Ctx& c) {
 
 }  // namespace
 
+int local_blocks(const Ctx& c) { return std::max(1, std::min(particle_blocks(c), c.sms * 2)); }
+
 int particle_blocks(const Ctx& c) {
     int64_t b = (c.np + THREADS - 1) / THREADS;
     int64_t cap = (int64_t)c.sms * 8;
@@ -700,7 +816,8 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
     if (!commit) cudaMemsetAsync(c.creep_count, 0, sizeof(int), c.stream);
 #define PIC_PUSH(Q, C, D)                                                                                        \
     k_push<Q, C, D><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.xi_new, c.P_new, \
-                                                  c.creep_list, c.creep_count, c.partials, c.dev_status)
+                                                  c.creep_list, c.creep_count, commit ? c.slide : nullptr,    \
+                                                  c.partials, c.dev_status)
     if (!commit) {
         if (closed) PIC_PUSH(0, false, false);
         else PIC_PUSH(1, false, false);
@@ -714,13 +831,15 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
 #undef PIC_PUSH
     ++c.launches;
     if (!commit && c.cfg.picard_accel) {
-        int lb = std::max(1, std::min(nb, c.sms * 2));
+        int lb = local_blocks(c);
         if (closed)
-            k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.creep_list,
-                                                     c.creep_count, c.dev_status);
+            k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
+                                                     c.creep_list, c.creep_count, c.slide, c.partials,
+                                                     c.dev_status);
         else
-            k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.creep_list,
-                                                     c.creep_count, c.dev_status);
+            k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
+                                                     c.creep_list, c.creep_count, c.slide, c.partials,
+                                                     c.dev_status);
         ++c.launches;
     }
 }
@@ -755,6 +874,23 @@ void launch_sort(Ctx& c) {
     std::swap(c.P, c.P_new);
     std::swap(c.vprev, c.vit);
     std::swap(c.id, c.id_tmp);
+}
+
+// g[c, list[k]] = gsave[c, list[k]] for the particles solved locally in the last iteration.
+__global__ void k_patch_local(int64_t np, const int32_t* __restrict__ list, const int* __restrict__ count,
+                              const double* __restrict__ gsave, double* __restrict__ g) {
+    const int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int64_t i = list[k];
+        g[i] = gsave[i];
+        g[np + i] = gsave[np + i];
+        g[2 * np + i] = gsave[2 * np + i];
+    }
+}
+
+void launch_patch_local(Ctx& c, double* g) {
+    k_patch_local<<<std::max(1, c.sms), THREADS, 0, c.stream>>>(c.np, c.creep_list, c.creep_count, c.gsave, g);
+    ++c.launches;
 }
 
 void launch_unpermute(Ctx& c, const double* src, double* dst, double s0, double s1, double s2) {

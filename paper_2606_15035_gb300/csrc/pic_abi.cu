@@ -223,6 +223,8 @@ pic_status allocate(pic_ctx* ctx) {
     ALLOC(c.P_new, double, np3);
     ALLOC(c.sort_tmp, double, np3);
     ALLOC(c.creep_list, int32_t, std::max<int64_t>(c.np, 1));
+    ALLOC(c.gsave, double, np3);
+    ALLOC(c.slide, uint8_t, std::max<int64_t>(c.np, 1));
     ALLOC(c.creep_count, int, 1);
     ALLOC(c.id, int64_t, std::max<int64_t>(c.np, 1));
     ALLOC(c.id_tmp, int64_t, std::max<int64_t>(c.np, 1));
@@ -322,6 +324,7 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
     if (diag) queue_energy(c);
     launch_rhs0(c);
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
+    if (np > 0) cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // sliding marks live one step
     int cur = 0, prev = 1, next = 2;
     cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
     {
@@ -340,8 +343,11 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
             launch_push(c, c.vit, c.vnew, c.J[next], false, false);
         }
         launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
+        if (c.cfg.picard_accel) launch_finalize(c, S_EVL_NUM, 2, local_blocks(c), false);
         launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
         if (c.prof) launch_finalize(c, S_PIECES_PUSH, 2, particle_blocks(c), false);
+        c.last_v = c.vit;
+        c.last_g = c.vnew;
         pic_status s = sync_results(ctx, "pic_step");
         if (s != PIC_OK) return s;
         const double* r = c.host_results;
@@ -350,7 +356,14 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
             c.prof_acc.scatter_pieces += (int64_t)r[S_PIECES_SCATTER];
         }
         if (p == 0) jscale = std::sqrt((double)N) * std::fabs(c.q) * r[S_JSCALE] / c.volume;
-        e_v = r[S_EV_DEN] > 0.0 ? std::sqrt(r[S_EV_NUM] / r[S_EV_DEN]) : 0.0;
+        {
+            double num = r[S_EV_NUM], den = r[S_EV_DEN];
+            if (c.cfg.picard_accel) {
+                num += r[S_EVL_NUM];
+                den += r[S_EVL_DEN];
+            }
+            e_v = den > 0.0 ? std::sqrt(num / den) : 0.0;
+        }
         {
             double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
             e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
@@ -374,6 +387,7 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
         last->e_v = e_v;
         last->e_J = e_J;
     }
+    c.last_failed = !converged;
     if (!converged && !c.cfg.accept_unconverged) {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "pic_step: Picard not converged after %d iterations (e_v=%.3e, e_J=%.3e)",
@@ -646,7 +660,10 @@ pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, co
     cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
     if (np > 0) launch_first_scatter(c, c.J[0], vgiven);
     mesh_phase(c, c.J[0], nullptr);
-    if (np > 0) launch_push(c, c.vit, c.vnew, nullptr, true, false);
+    if (np > 0) {
+        cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // no local solves in a single body
+        launch_push(c, c.vit, c.vnew, nullptr, true, false);
+    }
     pic_status s = sync_results(ctx, "pic_iterate");
     if (s != PIC_OK) return s;
     if (out->J) cudaMemcpyAsync(out->J, c.J[0], sizeof(double) * 3 * N, kout, c.stream);
@@ -668,6 +685,36 @@ pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, co
     }
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_iterate");
     return check_cuda(ctx, "pic_iterate");
+}
+
+pic_status pic_get_positions(pic_ctx* ctx, double* xi, int32_t on_device) {
+    if (!ctx || !xi) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.np == 0) return PIC_OK;
+    launch_unpermute(c, c.xi, c.sort_tmp, 1.0, 1.0, 1.0);
+    cudaMemcpyAsync(xi, c.sort_tmp, sizeof(double) * 3 * c.np,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_positions");
+    return check_cuda(ctx, "pic_get_positions");
+}
+
+pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t on_device) {
+    if (!ctx || !v_iter || !g_iter) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.np == 0) return PIC_OK;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!c.last_v || !c.last_g || !c.last_failed)
+        return fail(ctx, PIC_ERR_ARG, "pic_get_iterate: only available after a pic_step that did not converge");
+    // the image G(v^p): the next iterate with the locally solved particles' plain image
+    // restored, assembled in P_new (3 * np, unused between steps)
+    cudaMemcpyAsync(c.P_new, c.last_g, sizeof(double) * 3 * c.np, cudaMemcpyDeviceToDevice, c.stream);
+    if (c.cfg.picard_accel) launch_patch_local(c, c.P_new);
+    launch_unpermute(c, c.P_new, c.sort_tmp, 1.0, 1.0, 1.0);
+    cudaMemcpyAsync(g_iter, c.sort_tmp, sizeof(double) * 3 * c.np, kind, c.stream);
+    launch_unpermute(c, c.last_v, c.sort_tmp, 1.0, 1.0, 1.0);
+    cudaMemcpyAsync(v_iter, c.sort_tmp, sizeof(double) * 3 * c.np, kind, c.stream);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_iterate");
+    return check_cuda(ctx, "pic_get_iterate");
 }
 
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out) {

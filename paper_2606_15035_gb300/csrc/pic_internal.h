@@ -18,6 +18,8 @@ namespace pic {
 enum Slot : int {
     S_EV_NUM = 0,  // sum |v^{p+1} - v^p|^2
     S_EV_DEN,      // sum |v^{p+1}|^2
+    S_EVL_NUM,     // the same two sums over the locally solved particles (k_local)
+    S_EVL_DEN,
     S_EJ_NUM,      // sum |J^p - J^{p-1}|^2
     S_EJ_DEN,      // sum |J^p|^2
     S_JSCALE,      // sum |v^n|
@@ -71,6 +73,10 @@ struct Ctx {
     // particles, FP64 SoA (3 * np each)
     double *xi = nullptr, *v = nullptr, *P = nullptr, *vprev = nullptr;
     double *vit = nullptr, *vnew = nullptr, *xi_new = nullptr, *P_new = nullptr;
+    const double *last_v = nullptr, *last_g = nullptr;   // last Picard iterate and the next one
+    double* gsave = nullptr;         // G(v^p) of the locally solved particles (diagnostics)
+    bool last_failed = false;        // the last step hit picard_max
+    uint8_t* slide = nullptr;        // per particle, bit a: component a slides along a knot
     int32_t* creep_list = nullptr;   // creeping particles of the current iteration (local solves)
     int* creep_count = nullptr;
     int64_t *id = nullptr, *id_tmp = nullptr;
@@ -120,6 +126,7 @@ void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null);
 void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag);
 void launch_kinetic(Ctx& c);
 void launch_unpermute(Ctx& c, const double* src_soa3, double* dst_soa3, double scale0, double scale1, double scale2);
+void launch_patch_local(Ctx& c, double* g);
 void launch_permute_in(Ctx& c, const double* src_soa3, double* dst_soa3, double s0, double s1, double s2);
 void set_gauss_rule(int nq);
 
@@ -137,6 +144,7 @@ void launch_fill(Ctx& c, double* p, int64_t n, double value);
 void launch_scale_copy(Ctx& c, double* dst, const double* src, int64_t n, double s);
 
 int particle_blocks(const Ctx& c);
+int local_blocks(const Ctx& c);
 int mesh_blocks(const Ctx& c);
 
 }  // namespace pic

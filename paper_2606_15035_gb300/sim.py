@@ -151,6 +151,20 @@ def pic_profile(ctx, enable: bool, read: bool = True):
     return out
 
 
+def pic_get_iterate(ctx, npart):
+    """Last Picard iterate and its image G, each (np, 3) host arrays in pic_init order."""
+    a, b = np.zeros(3 * npart), np.zeros(3 * npart)
+    _check(_lib.lib().pic_get_iterate(ctx, _ptr(a), _ptr(b), 0), ctx)
+    return a.reshape(3, npart).T.copy(), b.reshape(3, npart).T.copy()
+
+
+def pic_get_positions(ctx, npart):
+    """Positions in cell units exactly as stored, (np, 3) host array in pic_init order."""
+    a = np.zeros(3 * npart)
+    _check(_lib.lib().pic_get_positions(ctx, _ptr(a), 0), ctx)
+    return a.reshape(3, npart).T.copy()
+
+
 def pic_last_error(ctx) -> str:
     return _lib.lib().pic_last_error(ctx).decode()
 
@@ -214,6 +228,12 @@ class PicSim:
 
     def energy(self) -> PicEnergy:
         return pic_energy(self.ctx)
+
+    def positions_cells(self):
+        return pic_get_positions(self.ctx, self.np)
+
+    def last_iterate(self):
+        return pic_get_iterate(self.ctx, self.np)
 
     def profile(self, enable=True, read=True):
         return pic_profile(self.ctx, enable, read)
