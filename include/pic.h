@@ -209,6 +209,41 @@ pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t
  * copied there (after synchronising the stream) and the accumulators are reset. */
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
 
+/* Largest mesh (nodes) accepted by pic_cn_update_static. */
+#define PIC_STATIC_MAX_CELLS 32768
+
+/* The Crank--Nicolson update of (phi, psi, A, U) for given sources, without allocating.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc where they need the update (a fixed, pre-committed device-memory budget, a
+ * host thread that must not enter the CUDA allocator because it can synchronise the device,
+ * or a plugin whose host application owns all device allocations).  It computes what
+ * pic_step's mesh phase computes, (I - a Delta_h) F^{n+1} = (I + a Delta_h) F^n + dt W^n +
+ * (dt^2 kappa^2 sigma / 2) src with a = kappa^2 dt^2 / 4 (src = rho_half for phi with sigma1,
+ * J for A with sigma2), by the same Chebyshev iteration, then W^{n+1} = 2 (F^{n+1} - F^n) / dt
+ * - W^n.
+ *
+ * Arguments: n, L: mesh nodes and box lengths (host); every array pointer is a DEVICE
+ * pointer in the library's mesh layout (x-fastest; A, U, J component-major, 3 * ncell).
+ * Inputs phi, psi, rho_half (ncell) and A, U, J (3 * ncell); outputs phi1, psi1 (ncell) and
+ * A1, U1 (3 * ncell), which must not overlap the inputs.  Work is queued on `stream`; the
+ * call returns without synchronising.
+ *
+ * Memory: working storage is one fixed __device__ array of 16 * PIC_STATIC_MAX_CELLS doubles
+ * (4 MiB) that every device loading the library holds until the process exits; no call
+ * allocates or frees device memory.  The first call on a device resolves that array's
+ * device address (cudaGetSymbolAddress) with the device current, so make it before any
+ * stream capture.  Every call on a device shares the array and nothing in it needs to start
+ * at zero (each call writes what it reads), but two calls whose work overlaps on the GPU
+ * (different streams, or before the earlier one finished) race on it.
+ *
+ * Errors: PIC_ERR_ARG for a null pointer, invalid sizes or constants, or
+ * n0 * n1 * n2 > PIC_STATIC_MAX_CELLS; PIC_ERR_CUDA if a launch or the set-up fails. */
+pic_status pic_cn_update_static(const int32_t n[3], const double L[3], double dt, double kappa, double sigma1,
+                                double sigma2, double helmholtz_tol, const double* phi, const double* psi,
+                                const double* A, const double* U, const double* rho_half, const double* J,
+                                double* phi1, double* psi1, double* A1, double* U1, void* stream);
+
 /* One-line description of the last error on this context ("" if none). */
 const char* pic_last_error(const pic_ctx* ctx);
 

@@ -29,8 +29,7 @@ PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
             "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile",
-            "pic_last_error",
-            "pic_destroy"]
+            "pic_cn_update_static", "pic_last_error", "pic_destroy"]
 
 
 class PicConfig(C.Structure):
@@ -164,6 +163,8 @@ def lib():
     L.pic_profile.argtypes = [C.c_void_p, C.c_int32, P(PicProfile)]
     L.pic_get_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    L.pic_cn_update_static.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_double, C.c_double,
+                                       C.c_double, C.c_double, C.c_double] + [C.c_void_p] * 10 + [C.c_void_p]
     L.pic_last_error.argtypes = [C.c_void_p]
     L.pic_last_error.restype = C.c_char_p
     L.pic_destroy.argtypes = [C.c_void_p]
