@@ -41,11 +41,12 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 SAMPLE_PARTICLES = 65536
 
 
-# Algorithmic FP64 flops of the fused push + next-orbit scatter kernel, counted from the
-# kernel source per particle and per knot-free orbit piece (see the design notes):
-FLOPS_PER_PARTICLE = 180
-FLOPS_PER_PUSH_PIECE = 660
-FLOPS_PER_SCATTER_PIECE = 225
+# Algorithmic FP64 flops (add, mul = 1, FMA = 2; the scatter's atomic adds counted) of the
+# fused push + next-orbit scatter kernel, counted from the kernel source per particle and per
+# knot-free orbit piece (see the design notes):
+FLOPS_PER_PARTICLE = 190
+FLOPS_PER_PUSH_PIECE = 409
+FLOPS_PER_SCATTER_PIECE = 150
 
 
 def parse():

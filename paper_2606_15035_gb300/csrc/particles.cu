@@ -53,7 +53,7 @@ __device__ __forceinline__ int scatter_closed(const StepParams& p, const double 
     return for_each_segment(x0, beta, true, [&](const Segment<double>& sg) {
         double I[8];
         int64_t g[8];
-        segment_weights8(sg, beta, I);
+        weights_from_ints(piece_integrals(sg, beta, false), I);
         segment_nodes8(sg, p.m, g);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -177,6 +177,48 @@ __device__ __forceinline__ void push_piece_closed(const StepParams& p, const Seg
     }
 }
 
+// The same piece contribution from the base integrals (no diagnostics).  For derivative
+// direction j with transverse axes (p, q), sum over the four transverse offsets (a, b) of
+// T0(a, b) D_ab with T0 = int w_{p,a} w_{q,b} and D_ab the difference across j of the nodes'
+// A^{(m)}.vbar, is D00 h + (D10 - D00) Sp + (D01 - D00) Sq + (D11 - D10 - D01 + D00) Spq;
+// the T1 (eta-weighted, C^{(m)}.vbar) sum has the same form with h^2/2, Ep, Eq, Epq.
+__device__ __forceinline__ void push_piece_fast(const StepParams& p, const Segment<double>& sg, const double beta[3],
+                                                const double vb[3], const double* __restrict__ table, PushAcc& acc) {
+    const PieceInts<double> I = piece_integrals(sg, beta, true);
+    double W[8];
+    weights_from_ints(I, W);
+    int64_t g[8];
+    segment_nodes8(sg, p.m, g);
+    const double s = sg.s0, oms = 1.0 - s, h = sg.h, hh2 = 0.5 * h * h;
+    double am[8], cc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double* t = table + 12 * g[k];
+        const double an = t[0] * vb[0] + t[1] * vb[1] + t[2] * vb[2];   // A^n_g . vbar
+        const double a1 = t[3] * vb[0] + t[4] * vb[1] + t[5] * vb[2];   // A^{n+1}_g . vbar
+        am[k] = oms * an + s * a1;                                       // A^{(m)}_nu . vbar
+        cc[k] = a1 - an;                                                 // C^{(m)}_nu . vbar
+        acc.gphi[0] += W[k] * t[6];
+        acc.gphi[1] += W[k] * t[7];
+        acc.gphi[2] += W[k] * t[8];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int pa = j == 0 ? 1 : 0, qa = j == 2 ? 1 : 2;              // transverse axes
+        const int sp = j == 0 ? 2 : 1, sq = j == 2 ? 2 : 4;              // their index strides
+        const int sj = j == 0 ? 1 : (j == 1 ? 2 : 4);                    // stride of axis j
+        const double D00 = am[sj] - am[0], D10 = am[sp + sj] - am[sp];
+        const double D01 = am[sq + sj] - am[sq], D11 = am[sp + sq + sj] - am[sp + sq];
+        const double C00 = cc[sj] - cc[0], C10 = cc[sp + sj] - cc[sp];
+        const double C01 = cc[sq + sj] - cc[sq], C11 = cc[sp + sq + sj] - cc[sp + sq];
+        const double t0 = D00 * h + (D10 - D00) * I.S1[pa] + (D01 - D00) * I.S1[qa] +
+                          (D11 - D10 - D01 + D00) * I.S2[j];
+        const double t1 = C00 * hh2 + (C10 - C00) * I.E1[pa] + (C01 - C00) * I.E1[qa] +
+                          (C11 - C10 - C01 + C00) * I.E2[j];
+        acc.F[j] += p.invH[j] * (t0 + t1);
+    }
+}
+
 template <bool DIAG>
 __device__ __forceinline__ void push_piece_gauss(const StepParams& p, const Segment<double>& sg, const double x0[3],
                                                  const double beta[3], const double vb[3],
@@ -259,7 +301,7 @@ __global__ void k_init_positions(StepParams p, const double* __restrict__ x, dou
     const int64_t np = p.np;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) xi[a * np + i] = wrap_pos(x[a * np + i] * p.invH[a], (double)p.m.n[a]);
+        for (int a = 0; a < 3; ++a) xi[a * np + i] = wrap_pos_any(x[a * np + i] * p.invH[a], (double)p.m.n[a]);
         id[i] = i;
     }
 }
@@ -348,8 +390,10 @@ __device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3
     }
     acc = PushAcc{};
     if constexpr (QUAD == 0) {
-        o.nseg = for_each_segment(x0, beta, true,
-                                  [&](const Segment<double>& sg) { push_piece_closed<DIAG>(p, sg, beta, vb, table, acc); });
+        o.nseg = for_each_segment(x0, beta, true, [&](const Segment<double>& sg) {
+            if constexpr (DIAG) push_piece_closed<true>(p, sg, beta, vb, table, acc);
+            else push_piece_fast(p, sg, beta, vb, table, acc);
+        });
     } else {
         o.nseg = for_each_segment(x0, beta, p.split != 0, [&](const Segment<double>& sg) {
             push_piece_gauss<DIAG>(p, sg, x0, beta, vb, table, acc);
@@ -362,7 +406,7 @@ __device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3
     }
     point_gather3(p, o.xe, table, 3, o.Ae);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) o.vw[a] = (o.Pw[a] - p.q * o.Ae[a]) / p.mass;
+    for (int a = 0; a < 3; ++a) o.vw[a] = (o.Pw[a] - p.q * o.Ae[a]) * p.inv_mass;
 }
 
 // The Algorithm 1 push for iterate vit, then either
@@ -765,6 +809,7 @@ StepParams make_params(const Ctx& c) {
     p.dt = c.cfg.dt;
     p.q = c.q;
     p.mass = c.mass;
+    p.inv_mass = 1.0 / c.mass;
     p.q_dV = c.q / c.dV;
     p.np = c.np;
     p.split = c.cfg.split_orbit_at_knots;

@@ -35,10 +35,19 @@ __device__ __forceinline__ int64_t node_index(int ix, int iy, int iz, const Mesh
     return (int64_t)ix + (int64_t)m.n[0] * ((int64_t)iy + (int64_t)m.n[1] * iz);
 }
 
+// Wrap any position onto [0, n) (initial data).
 template <typename T>
-__device__ __forceinline__ T wrap_pos(T x, T n) {
+__device__ __forceinline__ T wrap_pos_any(T x, T n) {
     T w = x - n * floor(x / n);
     return w >= n ? w - n : w;
+}
+
+// Wrap onto [0, n) a position that is less than one box length outside it (an orbit
+// moves far less than n cells per step).
+template <typename T>
+__device__ __forceinline__ T wrap_pos(T x, T n) {
+    T w = x < T(0) ? x + n : (x >= n ? x - n : x);
+    return w >= n ? w - n : (w < T(0) ? T(0) : w);
 }
 
 // One knot-free piece [s0, s0 + h] of an orbit: the stencil cell containing its midpoint
@@ -66,14 +75,15 @@ __device__ __forceinline__ int for_each_segment(const T xi0[3], const T beta[3],
         snext[a] = T(2);
         knot[a] = T(0);
         step[a] = T(0);
+        // the division is only needed when the orbit reaches the first knot ahead
         if (split && beta[a] > T(0)) {
             knot[a] = floor(xi0[a]) + T(1);
             step[a] = T(1);
-            snext[a] = (knot[a] - xi0[a]) / beta[a];
+            if (knot[a] - xi0[a] < beta[a]) snext[a] = (knot[a] - xi0[a]) / beta[a];
         } else if (split && beta[a] < T(0)) {
             knot[a] = ceil(xi0[a]) - T(1);
             step[a] = T(-1);
-            snext[a] = (knot[a] - xi0[a]) / beta[a];
+            if (knot[a] - xi0[a] > beta[a]) snext[a] = (knot[a] - xi0[a]) / beta[a];
         }
         if (!(snext[a] < T(1))) snext[a] = T(2);
     }
@@ -99,7 +109,8 @@ __device__ __forceinline__ int for_each_segment(const T xi0[3], const T beta[3],
         for (int a = 0; a < 3; ++a) {
             if (snext[a] == s1) {
                 knot[a] += step[a];
-                T sn = (knot[a] - xi0[a]) / beta[a];
+                const T dk = knot[a] - xi0[a];
+                T sn = (beta[a] > T(0) ? dk < beta[a] : dk > beta[a]) ? dk / beta[a] : T(2);
                 snext[a] = sn < T(1) ? sn : T(2);
             }
         }
@@ -173,6 +184,63 @@ __device__ __forceinline__ void segment_weights8(const Segment<T>& sg, const T b
 #pragma unroll
             for (int nz = 0; nz < 2; ++nz) I[nx + 2 * ny + 4 * nz] = segment_weight(qxy, pz.L[nz], pz.M[nz], sg.h);
         }
+}
+
+// Base integrals of one piece.  With w_a(eta) = r_a + beta_a eta the "upper" linear weight
+// of axis a (w_{a,1} of Appendix A; w_{a,0} = 1 - w_a):
+//   S1[a] = int_0^h w_a,   E1[a] = int_0^h eta w_a,
+//   S2[j] = int_0^h w_p w_q,   E2[j] = int_0^h eta w_p w_q   ((p, q) = the axes other than j),
+//   S3 = int_0^h w_x w_y w_z.
+// Every closed-form integral of Appendices A and B is a signed sum of these, because each
+// w_{a,0} = 1 - w_{a,1} (inclusion--exclusion).
+template <typename T>
+struct PieceInts {
+    T h, S1[3], E1[3], S2[3], E2[3], S3;
+};
+
+template <typename T>
+__device__ __forceinline__ PieceInts<T> piece_integrals(const Segment<T>& sg, const T beta[3], bool with_eta) {
+    PieceInts<T> I;
+    const T h = sg.h, h2 = h * h, h3 = h2 * h;
+    I.h = h;
+    const T c2 = T(0.5), c3 = T(1) / T(3), c4 = T(0.25);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        I.S1[a] = sg.r[a] * h + beta[a] * (c2 * h2);
+        I.E1[a] = with_eta ? sg.r[a] * (c2 * h2) + beta[a] * (c3 * h3) : T(0);
+    }
+    T d0[3], d1[3], d2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int p = j == 0 ? 1 : 0, q = j == 2 ? 1 : 2;
+        d0[j] = sg.r[p] * sg.r[q];
+        d1[j] = sg.r[p] * beta[q] + beta[p] * sg.r[q];
+        d2[j] = beta[p] * beta[q];
+        I.S2[j] = h * (d0[j] + h * (c2 * d1[j] + h * (c3 * d2[j])));
+        I.E2[j] = with_eta ? h2 * (c2 * d0[j] + h * (c3 * d1[j] + h * (c4 * d2[j]))) : T(0);
+    }
+    // w_x w_y w_z = (d0 + d1 eta + d2 eta^2)_{xy} (r_z + beta_z eta)
+    const T e0 = d0[2] * sg.r[2];
+    const T e1 = d1[2] * sg.r[2] + d0[2] * beta[2];
+    const T e2 = d2[2] * sg.r[2] + d1[2] * beta[2];
+    const T e3 = d2[2] * beta[2];
+    I.S3 = h * (e0 + h * (c2 * e1 + h * (c3 * e2 + h * (c4 * e3))));
+    return I;
+}
+
+// The eight weights I_nu of Appendix A from the base integrals, nu = nx + 2 ny + 4 nz.
+template <typename T>
+__device__ __forceinline__ void weights_from_ints(const PieceInts<T>& I, T W[8]) {
+    const T Sx = I.S1[0], Sy = I.S1[1], Sz = I.S1[2];
+    const T Syz = I.S2[0], Sxz = I.S2[1], Sxy = I.S2[2], Sxyz = I.S3;
+    W[7] = Sxyz;                       // (1,1,1)
+    W[3] = Sxy - Sxyz;                 // (1,1,0)
+    W[5] = Sxz - Sxyz;                 // (1,0,1)
+    W[6] = Syz - Sxyz;                 // (0,1,1)
+    W[1] = Sx - Sxy - W[5];            // (1,0,0)
+    W[2] = Sy - Syz - W[3];            // (0,1,0)
+    W[4] = Sz - Sxz - W[6];            // (0,0,1)
+    W[0] = I.h - Sx - Sy - Sz + Sxy + Sxz + Syz - Sxyz;   // (0,0,0)
 }
 
 template <typename T>

@@ -50,7 +50,7 @@ constexpr int THREADS = 256;
 struct StepParams {
     MeshDims m;
     double H[3], invH[3];
-    double dt, q, mass, q_dV;  // q_dV = q / dV
+    double dt, q, mass, inv_mass, q_dV;  // q_dV = q / dV
     int64_t np;
     int split;                 // split orbits at knots
     int nq;                    // Gauss points (Gauss quadrature only)
