@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -189,7 +190,8 @@ def main():
         pg = dist
     w = pi.WORKLOADS[args.workload]
     x, v, q, m = pi.workload_particles(w, run=rank)
-    cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol)
+    cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
+                                 precision=1 if args.precision == "mixed" else 0)
     s = sim.PicSim(cfg, x, v, q, m)
     stream = torch.cuda.current_stream()
     e0 = s.energy().total
@@ -276,12 +278,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.n), "particles_per_gpu": w.n_particles, "dt": w.dt,
-                       "picard_tol": w.picard_tol, "precision": "fp64", "orbits": "split at knots, closed form",
+                       "picard_tol": w.picard_tol,
+                       "precision": "fp64" if args.precision == "fp64" else
+                                    "mixed: FP32 iterations, FP64 refinement and final sweep",
+                       "orbits": "split at knots, closed form",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (particle state 0.3 GB per GPU)",
                        "mean_picard_iterations": info.total_iterations / max(info.steps_done, 1),
+                       "mean_fp32_iterations": info.total_iterations_fp32 / max(info.steps_done, 1),
                        "relative_energy_drift": drift},
             "roofline": roofline,
             "cpu_baseline": cpu,

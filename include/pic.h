@@ -70,7 +70,10 @@ typedef struct {
     int32_t split_orbit_at_knots; /* 1: split at every crossed knot (conservative); 0: unsplit (Gauss only) */
     int32_t quadrature;           /* PIC_QUAD_CLOSED (Appendices A/B) or PIC_QUAD_GAUSS (§4.7) */
     int32_t nq;                   /* Gauss points per piece when quadrature = PIC_QUAD_GAUSS (1..16) */
-    int32_t precision;            /* PIC_FP64 (mixed precision is selected by this field as well) */
+    int32_t precision;            /* PIC_FP64, or PIC_MIXED: the first Picard iterations of each step
+                                     in FP32 (orbit integrals, push, scatter; mesh solve and sums in
+                                     FP64), then FP64 iterations to picard_tol and the FP64 final
+                                     sweep; needs n_a <= 1024 */
     int32_t sort_every;           /* re-sort particles by cell every k steps (0: never) */
     int32_t diagnostics;          /* 1: accumulate the §5.1-§5.3 diagnostics during each step */
     int32_t accept_unconverged;   /* 1: commit a step that hit p_max (Algorithm 1 as printed) */
@@ -80,6 +83,8 @@ typedef struct {
                                      §4.8); all others, and every particle when 0, take the plain
                                      update v^{p+1} = G(v^p) of Algorithm 1 */
     double helmholtz_tol;         /* target error reduction of the CN Helmholtz solve (Chebyshev) */
+    double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v, e_J <= this */
+    int32_t mixed_max32;          /* PIC_MIXED: at most this many FP32 iterations per step */
 } pic_config;
 
 /* Initial particles of one species. */
@@ -105,6 +110,8 @@ typedef struct {
     int32_t converged;    /* 1 if the last step met picard_tol */
     int32_t total_iterations; /* Picard iterations summed over the committed steps */
     double e_v, e_J;      /* the last step's final velocity and current fixed-point errors */
+    int32_t iterations_fp32;       /* of the last step's iterations, those run in FP32 (PIC_MIXED) */
+    int32_t total_iterations_fp32; /* FP32 iterations summed over the committed steps */
 } pic_step_info;
 
 typedef struct {
@@ -161,11 +168,14 @@ typedef struct {
     int64_t particle_pushes;     /* sum over push launches of the particle count */
     int64_t push_pieces;         /* knot-free orbit pieces integrated by those pushes */
     int64_t scatter_pieces;      /* orbit pieces integrated by their next-orbit scatters */
+    int64_t push32_launches;     /* FP32 push + scatter launches (PIC_MIXED) */
+    double push32_ms;
 } pic_profile_t;
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
- * diagnostics off, local solves on, Chebyshev reduction 1e-17. */
+ * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-6,
+ * at most 8 FP32 iterations. */
 pic_status pic_config_default(pic_config* cfg);
 
 /* Create a context: copies the particles to the device, sorts them by cell, deposits

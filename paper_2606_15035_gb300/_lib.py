@@ -52,6 +52,8 @@ class PicConfig(C.Structure):
         ("accept_unconverged", C.c_int32),
         ("picard_accel", C.c_int32),
         ("helmholtz_tol", C.c_double),
+        ("mixed_tol32", C.c_double),
+        ("mixed_max32", C.c_int32),
     ]
 
 
@@ -82,6 +84,8 @@ class PicStepInfo(C.Structure):
         ("total_iterations", C.c_int32),
         ("e_v", C.c_double),
         ("e_J", C.c_double),
+        ("iterations_fp32", C.c_int32),
+        ("total_iterations_fp32", C.c_int32),
     ]
 
 
@@ -136,6 +140,8 @@ class PicProfile(C.Structure):
         ("particle_pushes", C.c_int64),
         ("push_pieces", C.c_int64),
         ("scatter_pieces", C.c_int64),
+        ("push32_launches", C.c_int64),
+        ("push32_ms", C.c_double),
     ]
 
 

@@ -142,6 +142,7 @@ void prof_resolve(Ctx& c) {
             case PH_SCATTER: c.prof_acc.scatter_ms += ms; c.prof_acc.scatter_launches += 1; break;
             case PH_MESH: c.prof_acc.mesh_ms += ms; break;
             case PH_SORT: c.prof_acc.sort_ms += ms; break;
+            case PH_PUSH32: c.prof_acc.push32_ms += ms; c.prof_acc.push32_launches += 1; break;
             default: break;
         }
         c.ev_pool.push_back(pe.second.first);
@@ -176,7 +177,12 @@ pic_status validate(const pic_config* cfg) {
     if (cfg->quadrature != PIC_QUAD_CLOSED && cfg->quadrature != PIC_QUAD_GAUSS) return PIC_ERR_ARG;
     if (cfg->quadrature == PIC_QUAD_CLOSED && !cfg->split_orbit_at_knots) return PIC_ERR_ARG;
     if (cfg->quadrature == PIC_QUAD_GAUSS && (cfg->nq < 1 || cfg->nq > 16)) return PIC_ERR_ARG;
-    if (cfg->precision != PIC_FP64) return PIC_ERR_ARG;
+    if (cfg->precision != PIC_FP64 && cfg->precision != PIC_MIXED) return PIC_ERR_ARG;
+    if (cfg->precision == PIC_MIXED) {
+        if (cfg->quadrature != PIC_QUAD_CLOSED || cfg->n[0] > 1024 || cfg->n[1] > 1024 || cfg->n[2] > 1024)
+            return PIC_ERR_ARG;
+        if (!(cfg->mixed_tol32 > 0.0) || cfg->mixed_max32 < 1) return PIC_ERR_ARG;
+    }
     if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
     return PIC_OK;
 }
@@ -245,6 +251,15 @@ pic_status allocate(pic_ctx* ctx) {
     ALLOC(c.rhs, double, 4 * N);
     for (int k = 0; k < 3; ++k) ALLOC(c.J[k], double, 3 * N);
     ALLOC(c.table, double, 12 * N);
+    if (c.cfg.precision == PIC_MIXED) {
+        ALLOC(c.cell32, int32_t, std::max<int64_t>(c.np, 1));
+        ALLOC(c.off32, float, np3);
+        ALLOC(c.v32, float, np3);
+        ALLOC(c.P32, float, np3);
+        ALLOC(c.vit32, float, np3);
+        ALLOC(c.vnew32, float, np3);
+        ALLOC(c.table32, float, 12 * N);
+    }
     ALLOC(c.partials, double, (size_t)NSLOT * MAX_BLOCKS);
     ALLOC(c.results, double, NSLOT);
     ALLOC(c.dev_status, int, 1);
@@ -326,16 +341,62 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
     if (np > 0) cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // sliding marks live one step
     int cur = 0, prev = 1, next = 2;
+    // PIC_MIXED: the iterations run in FP32 until they reach mixed_tol32 (or stop improving),
+    // then in FP64 from the FP32 iterate.
+    bool fp32 = c.cfg.precision == PIC_MIXED && np > 0;
+    int p32 = 0;
+    double e_v32_prev = INFINITY;
     cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
     {
         ProfScope ps(c, PH_SCATTER);
-        launch_first_scatter(c, c.J[cur], nullptr);
+        if (fp32) {
+            launch_to32(c);
+            launch_scatter32(c, c.J[cur]);
+        } else {
+            launch_first_scatter(c, c.J[cur], nullptr);
+        }
     }
     launch_finalize(c, S_JSCALE, 1, particle_blocks(c), false);
     bool converged = false;
     double e_v = 0.0, e_J = 0.0, jscale = 0.0;
     int p = 0;
     for (p = 0; p <= c.cfg.picard_max; ++p) {
+        if (fp32) {
+            mesh_phase(c, c.J[cur], p > 0 ? c.J[prev] : nullptr);
+            launch_table32(c);
+            cudaMemsetAsync(c.J[next], 0, sizeof(double) * 3 * N, c.stream);
+            {
+                ProfScope ps(c, PH_PUSH32);
+                launch_push32(c, c.J[next]);
+            }
+            launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
+            launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
+            pic_status s = sync_results(ctx, "pic_step (fp32)");
+            if (s != PIC_OK) return s;
+            const double* r = c.host_results;
+            if (p == 0) jscale = std::sqrt((double)N) * std::fabs(c.q) * r[S_JSCALE] / c.volume;
+            e_v = r[S_EV_DEN] > 0.0 ? std::sqrt(r[S_EV_NUM] / r[S_EV_DEN]) : 0.0;
+            {
+                double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
+                e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
+            }
+            if (!std::isfinite(e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
+            ++p32;
+            const bool reached = e_v <= c.cfg.mixed_tol32 && e_J <= c.cfg.mixed_tol32;
+            const bool stalled = p32 > 1 && e_v > 0.5 * e_v32_prev;
+            e_v32_prev = e_v;
+            std::swap(c.vit32, c.vnew32);
+            int old_prev = prev;
+            prev = cur;
+            cur = next;
+            next = old_prev;
+            if (reached || stalled || p32 >= c.cfg.mixed_max32) {
+                // continue in FP64 from the FP32 iterate, whose current is in J[cur]
+                launch_from32(c, c.vit32, c.vit);
+                fp32 = false;
+            }
+            continue;
+        }
         mesh_phase(c, c.J[cur], p > 0 ? c.J[prev] : nullptr);
         cudaMemsetAsync(c.J[next], 0, sizeof(double) * 3 * N, c.stream);
         {
@@ -383,6 +444,7 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
     }
     if (last) {
         last->iterations = std::min(p, c.cfg.picard_max) + 1;
+        last->iterations_fp32 = p32;
         last->converged = converged ? 1 : 0;
         last->e_v = e_v;
         last->e_J = e_J;
@@ -478,6 +540,8 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->diagnostics = 0;
     cfg->accept_unconverged = 0;
     cfg->picard_accel = 1;
+    cfg->mixed_tol32 = 1e-6;
+    cfg->mixed_max32 = 8;
     cfg->helmholtz_tol = 1e-17;
     return PIC_OK;
 }
@@ -565,8 +629,10 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps, pic_step_info* info) {
         if (s != PIC_OK) break;
         local.steps_done += 1;
         local.total_iterations += last.iterations;
+        local.total_iterations_fp32 += last.iterations_fp32;
     }
     local.iterations = last.iterations;
+    local.iterations_fp32 = last.iterations_fp32;
     local.converged = last.converged;
     local.e_v = last.e_v;
     local.e_J = last.e_J;

@@ -91,6 +91,11 @@ struct Ctx {
     double *J[3] = {nullptr, nullptr, nullptr};
     double* table = nullptr;             // 12 * ncell gather table
 
+    // FP32 working set of the mixed path (allocated only for PIC_MIXED)
+    int32_t* cell32 = nullptr;
+    float *off32 = nullptr, *v32 = nullptr, *P32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;
+    float* table32 = nullptr;            // 12 * ncell
+
     // reductions and status
     double *partials = nullptr, *results = nullptr;
     int* dev_status = nullptr;
@@ -116,7 +121,7 @@ struct Ctx {
     double K_n = 0, W_n = 0;
 };
 
-enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT };
+enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_PUSH32 };
 
 // ---- launchers (particles.cu) ----
 void launch_init_positions(Ctx& c, const double* x_dev);
@@ -129,6 +134,13 @@ void launch_unpermute(Ctx& c, const double* src_soa3, double* dst_soa3, double s
 void launch_patch_local(Ctx& c, double* g);
 void launch_permute_in(Ctx& c, const double* src_soa3, double* dst_soa3, double s0, double s1, double s2);
 void set_gauss_rule(int nq);
+
+// ---- launchers (particles32.cu) ----
+void launch_to32(Ctx& c);
+void launch_scatter32(Ctx& c, double* J);
+void launch_push32(Ctx& c, double* Jnext);
+void launch_table32(Ctx& c);
+void launch_from32(Ctx& c, const float* a, double* b);
 
 // ---- launchers (mesh.cu) ----
 void launch_rhs0(Ctx& c);

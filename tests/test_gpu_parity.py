@@ -41,6 +41,8 @@ def pair(sim, x, v, q, m, n, L, dt=0.1, tol=1e-13, **kw):
     if "picard_accel" in kw:
         okw["picard_accel"] = bool(kw["picard_accel"])
     ckw = dict(kw)
+    if "precision" in ckw:
+        ckw["precision"] = int(ckw["precision"])
     if "split" in ckw:
         ckw["split_orbit_at_knots"] = int(ckw.pop("split"))
     if ckw.get("quadrature") == "gauss":
@@ -320,4 +322,40 @@ def test_local_solves_match_oracle_where_plain_picard_cycles(sim):
     o1, oinfo = opic.step(o, ocfg)
     assert info.converged and oinfo["converged"]
     compare_state(s.get_state(), o1, ocfg, 1e-12, L)
+    s.close()
+
+
+def test_mixed_precision_steps_match_fp64_oracle(sim):
+    """PIC_MIXED: FP32 iterations then FP64 refinement to the same tolerance; the accepted
+    step solves the FP64 discrete equations, so it matches the FP64 oracle."""
+    x, v, q, m, n, L = c1_inputs()
+    s, ocfg = pair(sim, x, v, q, m, n, L, tol=1e-13, precision=1, diagnostics=1)
+    o = opic.init(x, v, q, m, ocfg)
+    for _ in range(4):
+        info = s.step(1)
+        o, oinfo = opic.step(o, ocfg)
+        assert info.converged and oinfo["converged"]
+        assert info.iterations_fp32 >= 1
+        compare_state(s.get_state(), o, ocfg, 1e-11, L)
+        d = s.diagnostics()
+        assert abs(d.R_total) <= 1e-13 * (d.K1 + d.W1) and d.RA_max <= 1e-15
+    s.close()
+
+
+def test_mixed_precision_full_c1_run(sim):
+    """The 8^3 x 8192 workload in PIC_MIXED for 50 steps: state within 1e-5 of the FP64 oracle
+    and relative energy drift within 1e-9 (the mixed-path targets)."""
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.workload_particles(w)
+    s, ocfg = pair(sim, x, v, q, m, w.n, w.L, dt=w.dt, tol=1e-12, precision=1)
+    ocfg = opic.Config(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol)
+    o = opic.init(x, v, q, m, ocfg)
+    e0 = s.energy().total
+    drift = 0.0
+    for _ in range(w.steps):
+        assert s.step(1).converged
+        drift = max(drift, abs(s.energy().total - e0) / e0)
+        o, oinfo = opic.step(o, ocfg)
+    compare_state(s.get_state(), o, ocfg, 1e-5, w.L)
+    assert drift <= 1e-9, drift
     s.close()
