@@ -47,6 +47,9 @@ SAMPLE_PARTICLES = 65536
 FLOPS_PER_PARTICLE = 190
 FLOPS_PER_PUSH_PIECE = 409
 FLOPS_PER_SCATTER_PIECE = 150
+# DRAM bytes (read + write) of one k_push launch on the 32^3 x 2.1M workload, from the ncu
+# capture summarised in profiles/k_push_fp64_twostream-32c-2M.md (this kernel version).
+KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 243.4e6}
 
 
 def parse():
@@ -59,6 +62,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -190,35 +194,41 @@ def main():
         pg = dist
     w = pi.WORKLOADS[args.workload]
     x, v, q, m = pi.workload_particles(w, run=rank)
-    cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
-                                 precision=1 if args.precision == "mixed" else 0)
-    s = sim.PicSim(cfg, x, v, q, m)
     stream = torch.cuda.current_stream()
-    e0 = s.energy().total
-    if args.warmup > 0:
-        s.step(args.warmup)
-    s.profile(True)                       # reset accumulators, profiling on
-    sampler = ClockSampler(local)
-    sampler.start()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    info = s.step(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    clocks = sampler.stop()
-    prof = s.profile(False)
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if pg:
-        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    e1 = s.energy().total
-    drift = abs(e1 - e0) / e0
+
+    def timed(precision, with_clocks):
+        """W warm-up steps, then K timed steps between barriers, CUDA events on the library's stream."""
+        cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
+                                     precision=1 if precision == "mixed" else 0)
+        sm = sim.PicSim(cfg, x, v, q, m)
+        e_start = sm.energy().total
+        if args.warmup > 0:
+            sm.step(args.warmup)
+        sm.profile(True)                  # reset accumulators, profiling on
+        sampler = ClockSampler(local) if with_clocks else None
+        if sampler:
+            sampler.start()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        inf = sm.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        clk = sampler.stop() if sampler else None
+        pr = sm.profile(False)
+        t_ms = ev0.elapsed_time(ev1)
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        if pg:
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        drift_ = abs(sm.energy().total - e_start) / e_start
+        return sm, inf, pr, float(t.item()), drift_, clk
+
+    s, info, prof, ms_max, drift, clocks = timed(args.precision, True)
+    ms = ms_max
     total_particles = w.n_particles * world
     value = total_particles * args.steps / (ms_max / 1e3)
 
@@ -230,7 +240,9 @@ def main():
     push_s = prof.push_ms / 1e3
     achieved = flops / push_s / 1e12 if push_s > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": KPUSH_TRAFFIC_BYTES.get(w.name) if args.precision == "fp64" else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": "k_push (fused orbit push + next-orbit current scatter, FP64)",
                 "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (derived; probe measured 1.203 TFLOP/s "
                              "at 2010 MHz)",
@@ -267,6 +279,28 @@ def main():
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e,
                "what": "pic_set_state from pinned host + pic_step(1) + pic_get_state to pinned host, per step"}
 
+    # the other precision on the same workload ("mixed vs FP64 at stated energy drift")
+    other = None
+    if args.precision == "fp64" and not args.no_mixed:
+        sm2, inf2, pr2, ms2, drift2, _ = timed("mixed", False)
+        sm2.close()
+        bytes32 = 64.0 * w.n_particles * pr2.push32_launches
+        hbm32 = bytes32 / (pr2.push32_ms / 1e3) / 1e9 if pr2.push32_ms > 0 else None
+        other = {
+            "precision": "mixed: FP32 iterations (cell index + FP32 offsets), FP64 refinement to the same tau "
+                         "and FP64 final sweep",
+            "value": total_particles * args.steps / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+            "relative_energy_drift": drift2,
+            "mean_picard_iterations": inf2.total_iterations / max(inf2.steps_done, 1),
+            "mean_fp32_iterations": inf2.total_iterations_fp32 / max(inf2.steps_done, 1),
+            "fp32_push_roofline": {"bound": "hbm", "achieved": hbm32, "peak": 6804.8, "unit": "GB/s",
+                                   "frac": (hbm32 / 6804.8) if hbm32 else None, "traffic": None,
+                                   "kernel": "k_push32 (FP32 orbit push + next-orbit scatter)",
+                                   "bytes_per_particle_iteration": 64},
+            "share_fp32_push": pr2.push32_ms / ms2 if ms2 > 0 else None,
+            "share_fp64_push": pr2.push_ms / ms2 if ms2 > 0 else None,
+        }
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cv, secs, mit, nsample = time_oracle(w, SAMPLE_PARTICLES, 1, 0)
@@ -295,6 +329,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(prof.launches),
             "clocks": clocks,
+            "mixed": other,
         }
         print(json.dumps(line))
     if pg:
