@@ -53,6 +53,8 @@ typedef enum {
     PIC_ERR_NO_CONVERGENCE = 4,  /* Picard reached picard_max without meeting picard_tol */
     PIC_ERR_NONFINITE = 5,       /* a non-finite residual or velocity appeared */
     PIC_ERR_SEGMENTS = 6,        /* an orbit crossed more knots in one step than supported */
+    PIC_ERR_INTERNAL = 7,        /* a device-side consistency check failed (a mesh-tile bound) */
+    PIC_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up (an asynchronous copy) */
 } pic_status;
 
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };

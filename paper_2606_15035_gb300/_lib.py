@@ -23,6 +23,8 @@ STATUS_NAMES = {
     4: "PIC_ERR_NO_CONVERGENCE",
     5: "PIC_ERR_NONFINITE",
     6: "PIC_ERR_SEGMENTS",
+    7: "PIC_ERR_INTERNAL",
+    8: "PIC_ERR_TIMEOUT",
 }
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1

@@ -165,6 +165,10 @@ pic_status sync_results(pic_ctx* ctx, const char* where) {
     if (st & DEV_ERR_SEGMENTS)
         return fail(ctx, PIC_ERR_SEGMENTS, std::string(where) + ": an orbit crossed more knots than supported in one step");
     if (st & DEV_ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, std::string(where) + ": non-finite particle velocity");
+    if (st & DEV_ERR_TIMEOUT)
+        return fail(ctx, PIC_ERR_TIMEOUT, std::string(where) + ": a bulk copy into shared memory did not complete");
+    if (st & DEV_ERR_TILE)
+        return fail(ctx, PIC_ERR_INTERNAL, std::string(where) + ": an orbit left the mesh tile of its block");
     return PIC_OK;
 }
 
@@ -252,12 +256,18 @@ pic_status allocate(pic_ctx* ctx) {
     for (int k = 0; k < 3; ++k) ALLOC(c.J[k], double, 3 * N);
     ALLOC(c.table, double, 12 * N);
     if (c.cfg.precision == PIC_MIXED) {
-        ALLOC(c.cell32, int32_t, std::max<int64_t>(c.np, 1));
-        ALLOC(c.off32, float, np3);
-        ALLOC(c.v32, float, np3);
-        ALLOC(c.P32, float, np3);
-        ALLOC(c.vit32, float, np3);
-        ALLOC(c.vnew32, float, np3);
+        // padded so that every chunk of 256 particles starts 16-byte aligned in every array
+        c.np32 = std::max<int64_t>((c.np + 255) / 256 * 256, 256);
+        ALLOC(c.cell32, int32_t, c.np32);
+        ALLOC(c.off32, float, 3 * c.np32);
+        ALLOC(c.v32, float, 3 * c.np32);
+        ALLOC(c.P32, float, 3 * c.np32);
+        ALLOC(c.vit32, float, 3 * c.np32);
+        ALLOC(c.vnew32, float, 3 * c.np32);
+        for (const void* q : {(const void*)c.cell32, (const void*)c.off32, (const void*)c.v32, (const void*)c.P32,
+                              (const void*)c.vit32, (const void*)c.vnew32})
+            if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
+                return fail(ctx, PIC_ERR_ARG, "the allocator returned a pointer that is not 16-byte aligned");
         ALLOC(c.table32, float, 12 * N);
     }
     ALLOC(c.partials, double, (size_t)NSLOT * MAX_BLOCKS);
@@ -369,7 +379,7 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
                 ProfScope ps(c, PH_PUSH32);
                 launch_push32(c, c.J[next]);
             }
-            launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
+            launch_finalize(c, S_EV_NUM, 2, push32_blocks(c), false);
             launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
             pic_status s = sync_results(ctx, "pic_step (fp32)");
             if (s != PIC_OK) return s;

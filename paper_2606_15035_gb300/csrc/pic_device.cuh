@@ -16,6 +16,8 @@ namespace pic {
 enum : int {
     DEV_ERR_SEGMENTS = 1,   // more knot crossings in one step than MAX_SEGMENTS allows
     DEV_ERR_NONFINITE = 2,  // a non-finite velocity or residual appeared
+    DEV_ERR_TILE = 4,       // an orbit left the mesh tile computed for its block (not expected)
+    DEV_ERR_TIMEOUT = 8,    // a bounded wait on an asynchronous copy gave up
 };
 
 constexpr int MAX_SEGMENTS = 64;

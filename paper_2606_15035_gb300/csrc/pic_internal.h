@@ -92,6 +92,7 @@ struct Ctx {
     double* table = nullptr;             // 12 * ncell gather table
 
     // FP32 working set of the mixed path (allocated only for PIC_MIXED)
+    int64_t np32 = 0;   // component stride of the FP32 arrays: np rounded up to 256 entries
     int32_t* cell32 = nullptr;
     float *off32 = nullptr, *v32 = nullptr, *P32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;
     float* table32 = nullptr;            // 12 * ncell
@@ -139,6 +140,7 @@ void set_gauss_rule(int nq);
 void launch_to32(Ctx& c);
 void launch_scatter32(Ctx& c, double* J);
 void launch_push32(Ctx& c, double* Jnext);
+int push32_blocks(const Ctx& c);   // grid of the FP32 chunk kernels (partials per block)
 void launch_table32(Ctx& c);
 void launch_from32(Ctx& c, const float* a, double* b);
 
