@@ -284,7 +284,8 @@ def main():
     if args.precision == "fp64" and not args.no_mixed:
         sm2, inf2, pr2, ms2, drift2, _ = timed("mixed", False)
         sm2.close()
-        bytes32 = 64.0 * w.n_particles * pr2.push32_launches
+        # per particle-iteration: read cell 4 + offset 12 + v^n 12 + increment 12, write 12
+        bytes32 = 52.0 * w.n_particles * pr2.push32_launches
         hbm32 = bytes32 / (pr2.push32_ms / 1e3) / 1e9 if pr2.push32_ms > 0 else None
         other = {
             "precision": "mixed: FP32 iterations (cell index + FP32 offsets), FP64 refinement to the same tau "
@@ -296,7 +297,7 @@ def main():
             "fp32_push_roofline": {"bound": "hbm", "achieved": hbm32, "peak": 6804.8, "unit": "GB/s",
                                    "frac": (hbm32 / 6804.8) if hbm32 else None, "traffic": None,
                                    "kernel": "k_push32 (FP32 orbit push + next-orbit scatter)",
-                                   "bytes_per_particle_iteration": 64},
+                                   "bytes_per_particle_iteration": 52},
             "share_fp32_push": pr2.push32_ms / ms2 if ms2 > 0 else None,
             "share_fp64_push": pr2.push_ms / ms2 if ms2 > 0 else None,
         }

@@ -85,7 +85,7 @@ typedef struct {
                                      §4.8); all others, and every particle when 0, take the plain
                                      update v^{p+1} = G(v^p) of Algorithm 1 */
     double helmholtz_tol;         /* target error reduction of the CN Helmholtz solve (Chebyshev) */
-    double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v, e_J <= this */
+    double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v <= this */
     int32_t mixed_max32;          /* PIC_MIXED: at most this many FP32 iterations per step */
 } pic_config;
 
@@ -176,7 +176,7 @@ typedef struct {
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
- * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-6,
+ * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
  * at most 8 FP32 iterations. */
 pic_status pic_config_default(pic_config* cfg);
 
@@ -220,6 +220,13 @@ pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t
 /* Switch live profiling on (1) or off (0).  If `out` is non-NULL the accumulated profile is
  * copied there (after synchronising the stream) and the accumulators are reset. */
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
+
+/* Residual history of the last pic_step call (the last step it ran): for each Picard
+ * iteration k, e_v[k] and e_J[k] (Algorithm 1's fixed-point errors, e_J = +inf at the first
+ * iteration) and fp32[k] = 1 if the iteration ran in FP32 (PIC_MIXED), else 0.  Writes at
+ * most `cap` entries into each non-NULL array and returns the number of iterations (which
+ * may exceed cap), or -1 for a NULL context. */
+int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32);
 
 /* Largest mesh (nodes) accepted by pic_cn_update_static. */
 #define PIC_STATIC_MAX_CELLS 32768

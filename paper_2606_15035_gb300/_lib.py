@@ -30,7 +30,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
-            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile",
+            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile", "pic_residual_history",
             "pic_cn_update_static", "pic_last_error", "pic_destroy"]
 
 
@@ -169,6 +169,8 @@ def lib():
     L.pic_set_state.argtypes = [C.c_void_p, P(PicStateView)]
     L.pic_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, P(PicIterateOut)]
     L.pic_profile.argtypes = [C.c_void_p, C.c_int32, P(PicProfile)]
+    L.pic_residual_history.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_int32)]
+    L.pic_residual_history.restype = C.c_int32
     L.pic_get_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_cn_update_static.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_double, C.c_double,

@@ -7,11 +7,16 @@
 // The FP64 kernels then refine the iterate to the FP64 tolerance and run the final sweep, so
 // the accepted step is a solution of the FP64 discrete equations.
 //
-// FP32 working set (device order, structure of arrays):
+// FP32 working set (device order, structure of arrays, component stride `stride`):
 //   cell[i]   packed cell index cx | cy << 10 | cz << 20 of the particle's start position;
 //   off[c,i]  offset of the start position inside that cell, in [0, 1) (cell units);
-//   v, P      v^n and P^n rounded to FP32;  vit, vnew: the Picard iterates.
+//   v         v^n rounded to FP32;
+//   vit, vnew the Picard iterates as increments dv = v^{n+1,p} - v^n.
 // Positions relative to the cell keep ~1e-7-cell resolution for the knot tests at any mesh size.
+// The iterates are increments because the push can produce them without P^n: the level-n
+// canonical momentum is P^n = m v^n + q A_h^n(x^n) (Eq. (orbit-push)), so
+//   m (v^{n+1} - v^n) = dt q (-grad phi_bar + (D A)^T v_bar) - q [A_h^{n+1}(x^{n+1}) - A_h^n(x^n)],
+// and every FP32 rounding then scales with the small increment instead of with v itself.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -243,12 +248,11 @@ __device__ __forceinline__ int scatter32(const MeshView<TILED>& mv, const int co
 }
 
 // G(u) in FP32: the orbit push of Algorithm 1 with the FP32 gather table
-// (per node: A^n (3), A^{n+1} (3), grad_h phi^{n+1/2} (3), 3 unused).  Returns in dP the
-// momentum change dt q (-grad phi_bar + (D A)^T v_bar) minus q A_h^{n+1}(x^{n+1}), so that
-// m v^{n+1} = P^n + dP.
+// (per node: A^n (3), A^{n+1} (3), grad_h phi^{n+1/2} (3), 3 unused).  Returns the
+// velocity increment dv = v^{n+1} - v^n of the pushed particle (see the file comment).
 template <bool TILED>
 __device__ __forceinline__ int push32(const Params32& p, const MeshView<TILED>& mv, const int co[3], const float x0[3],
-                                      const float beta[3], const float vb[3], float dP[3]) {
+                                      const float beta[3], const float vb[3], float dv[3]) {
     float gphi[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f};
     const int nseg = for_each_segment(x0, beta, true, [&](const Segment<float>& sg) {
         const PieceInts<float> I = piece_integrals(sg, beta, true);
@@ -288,34 +292,43 @@ __device__ __forceinline__ int push32(const Params32& p, const MeshView<TILED>& 
             F[j] += p.invH[j] * (t0 + t1);
         }
     });
-    // end point, in the particle's frame, then the point interpolant of A^{n+1}
-    int ce[3];
-    float r[3];
+    // dA = A_h^{n+1}(x^{n+1}) - A_h^n(x^n): point interpolants at the end and start points
+    float dA[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float xe = x0[a] + beta[a];
-        const float f = floorf(xe);
-        ce[a] = co[a] + (int)f;
-        r[a] = xe - f;
-    }
-    int g[8];
-    int64_t gg[8];
-    float Ae[3] = {0.f, 0.f, 0.f};
-    if (mv.nodes8(ce, g, gg)) {
+    for (int end = 0; end < 2; ++end) {
+        int ce[3];
+        float r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float xe = end ? x0[a] + beta[a] : x0[a];
+            const float f = floorf(xe);
+            ce[a] = co[a] + (int)f;
+            r[a] = xe - f;
+        }
+        int g[8];
+        int64_t gg[8];
+        if (!mv.nodes8(ce, g, gg)) continue;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const float wx = (k & 1) ? r[0] : 1.f - r[0], wy = (k & 2) ? r[1] : 1.f - r[1];
             const float wz = (k & 4) ? r[2] : 1.f - r[2];
             const float w = wx * wy * wz;
             const float4* t4 = mv.node(g, gg, k);
-            const float4 a = t4[0], b = t4[1];
-            Ae[0] += w * a.w;
-            Ae[1] += w * b.x;
-            Ae[2] += w * b.y;
+            const float4 a = t4[0];
+            if (end) {
+                const float4 b = t4[1];
+                dA[0] += w * a.w;
+                dA[1] += w * b.x;
+                dA[2] += w * b.y;
+            } else {
+                dA[0] -= w * a.x;
+                dA[1] -= w * a.y;
+                dA[2] -= w * a.z;
+            }
         }
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dP[a] = p.dt * (p.q * (F[a] - gphi[a])) - p.q * Ae[a];
+    for (int a = 0; a < 3; ++a) dv[a] = (p.dt * (p.q * (F[a] - gphi[a])) - p.q * dA[a]) * p.inv_mass;
     return nseg;
 }
 
@@ -348,11 +361,10 @@ __device__ __forceinline__ void flush_jtile(const Box& b, const int ref[3], cons
     }
 }
 
-// FP64 masters -> FP32 working set; v^{n+1,0} = 2 v^n - v^{n-1}.
+// FP64 masters -> FP32 working set; first iterate v^{n+1,0} = 2 v^n - v^{n-1}, as an increment.
 __global__ void k_to32(Params32 p, const double* __restrict__ xi, const double* __restrict__ v,
-                       const double* __restrict__ P, const double* __restrict__ vprev, int32_t* __restrict__ cell,
-                       float* __restrict__ off, float* __restrict__ v32, float* __restrict__ P32,
-                       float* __restrict__ vit32, double* __restrict__ partials) {
+                       const double* __restrict__ vprev, int32_t* __restrict__ cell, float* __restrict__ off,
+                       float* __restrict__ v32, float* __restrict__ vit32, double* __restrict__ partials) {
     __shared__ double sm[32];
     const int64_t np = p.np;
     double jsc = 0.0;
@@ -370,8 +382,7 @@ __global__ void k_to32(Params32 p, const double* __restrict__ xi, const double* 
             packed |= ((int32_t)c & CELL_MASK) << (a * CELL_BITS);
             const double vv = v[a * np + i];
             v32[a * p.stride + i] = (float)vv;
-            P32[a * p.stride + i] = (float)P[a * np + i];
-            vit32[a * p.stride + i] = (float)(2.0 * vv - vprev[a * np + i]);
+            vit32[a * p.stride + i] = (float)(vv - vprev[a * np + i]);   // (2 v^n - v^{n-1}) - v^n
         }
         cell[i] = packed;
     }
@@ -403,8 +414,8 @@ __device__ __forceinline__ Chunk chunk_of(int64_t ch, int64_t np, int32_t ref_ce
 
 // ---- TMA staging of a chunk's particle fields (cp.async.bulk + mbarrier) ------------------
 
-constexpr int NFIELD = 13;   // cell | offset (3) | v^n (3) | P^n (3) | iterate (3)
-constexpr int F_CELL = 0, F_OFF = 1, F_V = 4, F_P = 7, F_IT = 10;
+constexpr int NFIELD = 10;   // cell | offset (3) | v^n (3) | iterate increment (3)
+constexpr int F_CELL = 0, F_OFF = 1, F_V = 4, F_IT = 7;
 constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s: bound of every wait on a copy
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
@@ -466,9 +477,9 @@ __device__ __forceinline__ uint32_t chunk_bytes(int64_t ch, int64_t np) {
     return (uint32_t)((cnt * 4 + 15) & ~(int64_t)15);
 }
 
-// Issued by one thread: the 13 fields of chunk ch into buf, completing on bar.
+// Issued by one thread: the NFIELD fields of chunk ch into buf, completing on bar.
 __device__ __forceinline__ void stage_chunk(const Params32& p, int64_t ch, uint32_t* buf, uint64_t* bar,
-                                            const int32_t* cell, const float* off, const float* v32, const float* P32,
+                                            const int32_t* cell, const float* off, const float* v32,
                                             const float* vit32) {
     const int64_t base = ch * CHUNK32;
     const uint32_t bytes = chunk_bytes(ch, p.np);
@@ -479,7 +490,6 @@ __device__ __forceinline__ void stage_chunk(const Params32& p, int64_t ch, uint3
         const int64_t o = a * p.stride + base;
         bulk_load(buf + (F_OFF + a) * CHUNK32, off + o, bytes, bar);
         bulk_load(buf + (F_V + a) * CHUNK32, v32 + o, bytes, bar);
-        bulk_load(buf + (F_P + a) * CHUNK32, P32 + o, bytes, bar);
         bulk_load(buf + (F_IT + a) * CHUNK32, vit32 + o, bytes, bar);
     }
 }
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(CHUNK32) k_scatter32(Params32 p, const int32_t
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 x0[a] = off[a * p.stride + k.i];
-                const float vb = 0.5f * (vit32[a * p.stride + k.i] + v32[a * p.stride + k.i]);
+                const float vb = v32[a * p.stride + k.i] + 0.5f * vit32[a * p.stride + k.i];
                 beta[a] = p.dt * vb * p.invH[a];
                 w[a] = p.q_dV * vb;
             }
@@ -556,7 +566,6 @@ __global__ void __launch_bounds__(CHUNK32) k_scatter32(Params32 p, const int32_t
 __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, const int32_t* __restrict__ cell,
                                                                  const float* __restrict__ off,
                                                                  const float* __restrict__ v32,
-                                                                 const float* __restrict__ P32,
                                                                  const float* __restrict__ vit32,
                                                                  const float* __restrict__ table,
                                                                  float* __restrict__ vnew32,
@@ -578,7 +587,7 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0 && blockIdx.x < nchunks) stage_chunk(p, blockIdx.x, stage[0], &bar[0], cell, off, v32, P32, vit32);
+    if (tid == 0 && blockIdx.x < nchunks) stage_chunk(p, blockIdx.x, stage[0], &bar[0], cell, off, v32, vit32);
     float ev_num = 0.f, ev_den = 0.f;
     int it = 0;
     bool failed = false;
@@ -587,7 +596,7 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
         const bool more = ch + gridDim.x < nchunks;
         if (tid == 0 && more) {
             bulk_wait_read();      // the previous chunk's iterate store has left the other buffer
-            stage_chunk(p, ch + gridDim.x, stage[b ^ 1], &bar[b ^ 1], cell, off, v32, P32, vit32);
+            stage_chunk(p, ch + gridDim.x, stage[b ^ 1], &bar[b ^ 1], cell, off, v32, vit32);
         }
         if (!__syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1))) {
             // a copy did not complete: report, let the copies in flight land, stop this block
@@ -608,7 +617,7 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 x0[a] = fld(S, F_OFF + a, j);
-                vb[a] = 0.5f * (fld(S, F_IT + a, j) + fld(S, F_V + a, j));
+                vb[a] = fld(S, F_V + a, j) + 0.5f * fld(S, F_IT + a, j);
                 beta[a] = p.dt * vb[a] * p.invH[a];
             }
         }
@@ -630,30 +639,29 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
         __syncthreads();
         float bn[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
         if (k.valid) {
-            float dP[3];
+            float dv[3];
             int ns;
             if (tiled) {
                 MeshView<true> mv{tab, nullptr, {0.f, 0.f, 0.f}, nullptr, bx, p.m, status};
-                ns = push32(p, mv, co, x0, beta, vb, dP);
+                ns = push32(p, mv, co, x0, beta, vb, dv);
             } else {
                 MeshView<false> mv{table4, nullptr, {0.f, 0.f, 0.f}, nullptr, bx, p.m, status};
-                ns = push32(p, mv, cb, x0, beta, vb, dP);
+                ns = push32(p, mv, cb, x0, beta, vb, dv);
             }
             if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
-            float vw[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                vw[a] = (fld(S, F_P + a, j) + dP[a]) * p.inv_mass;
                 const float vn = fld(S, F_V + a, j);
-                const float d = vw[a] - fld(S, F_IT + a, j);
+                const float d = dv[a] - fld(S, F_IT + a, j);
+                const float vw = vn + dv[a];
                 ev_num += d * d;
-                ev_den += vw[a] * vw[a];
-                S[(F_IT + a) * CHUNK32 + j] = __float_as_uint(vw[a]);   // staged for the bulk store
-                const float vbn = 0.5f * (vw[a] + vn);
+                ev_den += vw * vw;
+                S[(F_IT + a) * CHUNK32 + j] = __float_as_uint(dv[a]);   // staged for the bulk store
+                const float vbn = vn + 0.5f * dv[a];
                 bn[a] = p.dt * vbn * p.invH[a];
                 w[a] = p.q_dV * vbn;
             }
-            if (!(isfinite(vw[0]) && isfinite(vw[1]) && isfinite(vw[2]))) atomicOr(status, DEV_ERR_NONFINITE);
+            if (!(isfinite(dv[0]) && isfinite(dv[1]) && isfinite(dv[2]))) atomicOr(status, DEV_ERR_NONFINITE);
         }
         chunk_scatter(p, k, cb, x0, bn, w, jt, sbox, Jnext, status);
         fence_async_smem();   // this thread's accesses to S come before the bulk copies that follow
@@ -681,12 +689,13 @@ __global__ void k_table32(int64_t N, const double* __restrict__ t64, float* __re
     }
 }
 
-// FP32 iterate (component stride `stride`) -> FP64 iterate (stride np).
-__global__ void k_from32(int64_t np, int64_t stride, const float* __restrict__ a, double* __restrict__ b) {
+// FP32 iterate increment (component stride `stride`) -> FP64 iterate v^n + dv (stride np).
+__global__ void k_from32(int64_t np, int64_t stride, const float* __restrict__ dv, const double* __restrict__ vn,
+                         double* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
-        b[i] = (double)a[i];
-        b[np + i] = (double)a[stride + i];
-        b[2 * np + i] = (double)a[2 * stride + i];
+        out[i] = vn[i] + (double)dv[i];
+        out[np + i] = vn[np + i] + (double)dv[stride + i];
+        out[2 * np + i] = vn[2 * np + i] + (double)dv[2 * stride + i];
     }
 }
 
@@ -706,8 +715,8 @@ Params32 make_params32(const Ctx& c) {
 }  // namespace
 
 void launch_to32(Ctx& c) {
-    k_to32<<<particle_blocks(c), THREADS, 0, c.stream>>>(make_params32(c), c.xi, c.v, c.P, c.vprev, c.cell32,
-                                                         c.off32, c.v32, c.P32, c.vit32, c.partials);
+    k_to32<<<particle_blocks(c), THREADS, 0, c.stream>>>(make_params32(c), c.xi, c.v, c.vprev, c.cell32,
+                                                         c.off32, c.v32, c.vit32, c.partials);
     ++c.launches;
 }
 
@@ -724,7 +733,7 @@ void launch_scatter32(Ctx& c, double* J) {
 }
 
 void launch_push32(Ctx& c, double* Jnext) {
-    k_push32<<<push32_blocks(c), CHUNK32, 0, c.stream>>>(make_params32(c), c.cell32, c.off32, c.v32, c.P32, c.vit32,
+    k_push32<<<push32_blocks(c), CHUNK32, 0, c.stream>>>(make_params32(c), c.cell32, c.off32, c.v32, c.vit32,
                                                            c.table32, c.vnew32, Jnext, c.partials, c.dev_status);
     ++c.launches;
 }
@@ -735,7 +744,7 @@ void launch_table32(Ctx& c) {
 }
 
 void launch_from32(Ctx& c, const float* a, double* b) {
-    k_from32<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.np32, a, b);
+    k_from32<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.np32, a, c.v, b);
     ++c.launches;
 }
 

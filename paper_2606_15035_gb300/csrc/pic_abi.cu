@@ -261,10 +261,9 @@ pic_status allocate(pic_ctx* ctx) {
         ALLOC(c.cell32, int32_t, c.np32);
         ALLOC(c.off32, float, 3 * c.np32);
         ALLOC(c.v32, float, 3 * c.np32);
-        ALLOC(c.P32, float, 3 * c.np32);
         ALLOC(c.vit32, float, 3 * c.np32);
         ALLOC(c.vnew32, float, 3 * c.np32);
-        for (const void* q : {(const void*)c.cell32, (const void*)c.off32, (const void*)c.v32, (const void*)c.P32,
+        for (const void* q : {(const void*)c.cell32, (const void*)c.off32, (const void*)c.v32,
                               (const void*)c.vit32, (const void*)c.vnew32})
             if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
                 return fail(ctx, PIC_ERR_ARG, "the allocator returned a pointer that is not 16-byte aligned");
@@ -351,6 +350,9 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
     if (np > 0) cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // sliding marks live one step
     int cur = 0, prev = 1, next = 2;
+    c.hist_ev.clear();
+    c.hist_eJ.clear();
+    c.hist_fp32.clear();
     // PIC_MIXED: the iterations run in FP32 until they reach mixed_tol32 (or stop improving),
     // then in FP64 from the FP32 iterate.
     bool fp32 = c.cfg.precision == PIC_MIXED && np > 0;
@@ -390,9 +392,14 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
                 double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
                 e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
             }
+            c.hist_ev.push_back(e_v);
+            c.hist_eJ.push_back(e_J);
+            c.hist_fp32.push_back(1);
             if (!std::isfinite(e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
             ++p32;
-            const bool reached = e_v <= c.cfg.mixed_tol32 && e_J <= c.cfg.mixed_tol32;
+            // e_J of iteration p measures the change that iteration p - 1 made to v, so e_v alone
+            // says that the FP32 iterate has reached the FP32 noise floor
+            const bool reached = e_v <= c.cfg.mixed_tol32;
             const bool stalled = p32 > 1 && e_v > 0.5 * e_v32_prev;
             e_v32_prev = e_v;
             std::swap(c.vit32, c.vnew32);
@@ -401,8 +408,14 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
             cur = next;
             next = old_prev;
             if (reached || stalled || p32 >= c.cfg.mixed_max32) {
-                // continue in FP64 from the FP32 iterate, whose current is in J[cur]
-                launch_from32(c, c.vit32, c.vit);
+                // continue in FP64 from the FP32 iterate; its current is recomputed in FP64 (the
+                // fixed-point rounding of the FP32 current would cost one more FP64 iteration)
+                launch_from32(c, c.vit32, c.vnew);   // vnew is free until the next push
+                cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
+                {
+                    ProfScope ps(c, PH_SCATTER);
+                    launch_first_scatter(c, c.J[cur], c.vnew);   // also copies the iterate into vit
+                }
                 fp32 = false;
             }
             continue;
@@ -439,6 +452,9 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
             double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
             e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
         }
+        c.hist_ev.push_back(e_v);
+        c.hist_eJ.push_back(e_J);
+        c.hist_fp32.push_back(0);
         if (!std::isfinite(e_v) || (p > 0 && !std::isfinite(e_J)))
             return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
         if (e_v <= c.cfg.picard_tol && e_J <= c.cfg.picard_tol) {
@@ -550,7 +566,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->diagnostics = 0;
     cfg->accept_unconverged = 0;
     cfg->picard_accel = 1;
-    cfg->mixed_tol32 = 1e-6;
+    cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
     cfg->helmholtz_tol = 1e-17;
     return PIC_OK;
@@ -806,6 +822,18 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out) {
     }
     c.prof = enable != 0;
     return check_cuda(ctx, "pic_profile");
+}
+
+int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32) {
+    if (!ctx) return -1;
+    const Ctx& c = ctx->c;
+    const int32_t n = (int32_t)c.hist_ev.size();
+    for (int32_t k = 0; k < n && k < cap; ++k) {
+        if (e_v) e_v[k] = c.hist_ev[k];
+        if (e_J) e_J[k] = c.hist_eJ[k];
+        if (fp32) fp32[k] = c.hist_fp32[k];
+    }
+    return n;
 }
 
 const char* pic_last_error(const pic_ctx* ctx) {

@@ -92,9 +92,11 @@ struct Ctx {
     double* table = nullptr;             // 12 * ncell gather table
 
     // FP32 working set of the mixed path (allocated only for PIC_MIXED)
+    std::vector<double> hist_ev, hist_eJ;   // residuals of the last step's iterations
+    std::vector<int32_t> hist_fp32;
     int64_t np32 = 0;   // component stride of the FP32 arrays: np rounded up to 256 entries
     int32_t* cell32 = nullptr;
-    float *off32 = nullptr, *v32 = nullptr, *P32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;
+    float *off32 = nullptr, *v32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;   // iterates: increments
     float* table32 = nullptr;            // 12 * ncell
 
     // reductions and status

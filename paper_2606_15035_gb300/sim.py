@@ -151,6 +151,18 @@ def pic_profile(ctx, enable: bool, read: bool = True):
     return out
 
 
+def pic_residual_history(ctx):
+    """Per-iteration (e_v, e_J, fp32) of the last step, as three 1-D numpy arrays."""
+    L = _lib.lib()
+    n = L.pic_residual_history(ctx, 0, None, None, None)
+    if n < 0:
+        raise ValueError("null context")
+    ev, ej, f32 = np.zeros(max(n, 1)), np.zeros(max(n, 1)), np.zeros(max(n, 1), dtype=np.int32)
+    L.pic_residual_history(ctx, n, ev.ctypes.data_as(C.POINTER(C.c_double)),
+                           ej.ctypes.data_as(C.POINTER(C.c_double)), f32.ctypes.data_as(C.POINTER(C.c_int32)))
+    return ev[:n], ej[:n], f32[:n]
+
+
 def pic_get_iterate(ctx, npart):
     """Last Picard iterate and its image G, each (np, 3) host arrays in pic_init order."""
     a, b = np.zeros(3 * npart), np.zeros(3 * npart)
@@ -237,6 +249,9 @@ class PicSim:
 
     def profile(self, enable=True, read=True):
         return pic_profile(self.ctx, enable, read)
+
+    def residual_history(self):
+        return pic_residual_history(self.ctx)
 
     def diagnostics(self) -> PicDiag:
         return pic_diagnostics(self.ctx)
