@@ -346,29 +346,12 @@ __global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, con
     write_partial<double>(partials, S_JSCALE, jsc, sm, false);
 }
 
-// Constants of the particle-local solve for "creeping" particles (see k_local).
-constexpr double BETA_CREEP = 0.1;   // cells
+// Constants of the particle-local solve for "creeping" particles (see k_local); the
+// classifier is_creeping and its BETA_CREEP / D_KNOT live in pic_device.cuh.
 constexpr int LOCAL_STEPS = 24;      // push evaluations per creeping particle
 constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
 constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
-constexpr double D_KNOT = 1e-6;      // cells: starting this close to a knot also counts
 constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes beta = d -+ SLIDE_PROBE
-
-// On an axis where the orbit moves less than BETA_CREEP cells, does it get within 2 |beta|
-// of the next knot ahead, or start within D_KNOT of any knot?  Those orbits cross a knot
-// while barely moving, nearly do, or hover on a knot (an iterate can flip between
-// crossing and not crossing).
-__device__ __forceinline__ bool is_creeping(const double x0[3], const double beta[3]) {
-    bool f = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double b = beta[a];
-        const double d = b > 0.0 ? floor(x0[a]) + 1.0 - x0[a] : x0[a] - (ceil(x0[a]) - 1.0);
-        const double near = fmin(x0[a] - floor(x0[a]), ceil(x0[a]) - x0[a]);
-        f |= (fabs(b) < BETA_CREEP) && (((b != 0.0) && (d < 2.0 * fabs(b))) || (near < D_KNOT));
-    }
-    return f;
-}
 
 struct PushOut {
     double Pw[3], xe[3], Ae[3], vw[3];

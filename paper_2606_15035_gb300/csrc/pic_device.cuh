@@ -289,6 +289,27 @@ __device__ __forceinline__ void point_weights8(const T xi[3], const MeshDims& m,
             }
 }
 
+// ---- "creeping" orbits --------------------------------------------------------------------
+
+constexpr double BETA_CREEP = 0.1;   // cells
+constexpr double D_KNOT = 1e-6;      // cells: starting this close to a knot also counts
+
+// On an axis where the orbit moves less than BETA_CREEP cells, does it get within 2 |beta|
+// of the next knot ahead, or start within D_KNOT of any knot?  Those orbits cross a knot
+// while barely moving, nearly do, or hover on a knot (an iterate can flip between
+// crossing and not crossing).
+__device__ __forceinline__ bool is_creeping(const double x0[3], const double beta[3]) {
+    bool f = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double b = beta[a];
+        const double d = b > 0.0 ? floor(x0[a]) + 1.0 - x0[a] : x0[a] - (ceil(x0[a]) - 1.0);
+        const double near = fmin(x0[a] - floor(x0[a]), ceil(x0[a]) - x0[a]);
+        f |= (fabs(b) < BETA_CREEP) && (((b != 0.0) && (d < 2.0 * fabs(b))) || (near < D_KNOT));
+    }
+    return f;
+}
+
 // ---- block reductions (fixed order, so results are reproducible for a fixed launch) ----
 
 template <typename T>

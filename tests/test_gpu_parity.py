@@ -359,3 +359,25 @@ def test_mixed_precision_full_c1_run(sim):
     compare_state(s.get_state(), o, ocfg, 1e-5, w.L)
     assert drift <= 1e-9, drift
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_history_records_each_iteration(sim, precision):
+    """pic_residual_history: one entry per Picard iteration of the last step, the last one
+    meeting the tolerance, FP32 entries (mixed path) first and no FP32 entry on the FP64
+    path; the FP64 iterations of a contracting step shrink e_v."""
+    x, v, q, m, n, L = c1_inputs()
+    s, _ = pair(sim, x, v, q, m, n, L, tol=1e-13, precision=precision)
+    s.step(2)
+    info = s.step(1)
+    ev, ej, f32 = s.residual_history()
+    assert len(ev) == info.iterations and len(ej) == len(ev)
+    assert int(f32.sum()) == info.iterations_fp32
+    assert (precision == 1) == (info.iterations_fp32 > 0)
+    if precision == 1:
+        k = int(f32.sum())
+        assert (f32[:k] == 1).all() and (f32[k:] == 0).all()
+    assert ev[-1] <= 1e-13 and ej[-1] <= 1e-13 and np.isinf(ej[0])
+    d = ev[f32 == 0]
+    assert d[-1] < d[0] or len(d) == 1
+    s.close()
