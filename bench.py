@@ -321,7 +321,8 @@ def main():
                                     "mixed: FP32 iterations, FP64 refinement and final sweep",
                        "orbits": "split at knots, closed form",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (particle state 0.3 GB per GPU)",
+                       "l2": f"inputs larger than L2 (FP64 particle state {w.n_particles * 120 / 1e9:.1f} GB "
+                             f"per GPU: x, v, P, v^(n-1), iterate)",
                        "mean_picard_iterations": info.total_iterations / max(info.steps_done, 1),
                        "mean_fp32_iterations": info.total_iterations_fp32 / max(info.steps_done, 1),
                        "relative_energy_drift": drift},
