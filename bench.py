@@ -173,11 +173,88 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def run_ensemble(args, world, rank, local):
+    """--workload ensemble-<R>: R independent runs (pic_inputs.ensemble_runs: meshes 16^3..48^3,
+    8..64 particles per cell, v0 in [0.1, 0.3], eps in [1e-4, 1e-2]) stepped together through
+    pic_ensemble_step, against the same runs stepped one after another with pic_step.  The
+    runs use their own streams, so the timed region is bracketed by device-wide
+    synchronisations and timed on the host clock."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import pic_inputs as pi
+    from paper_2606_15035_gb300 import sim
+
+    torch.cuda.set_device(local)
+    nruns = int(args.workload.split("-")[1])
+    runs = pi.ensemble_runs(nruns, seed=pi.twostream.ENSEMBLE_SEED + 1000 * rank)
+    prec = 1 if args.precision == "mixed" else 0
+    items = []
+    for r in runs:
+        x, v, q, m = pi.ensemble_particles(r)
+        items.append((sim.pic_config_default(n=r.n, L=r.L, dt=r.dt, picard_tol=r.picard_tol, precision=prec),
+                      x, v, q, m))
+    total = sum(r.n_particles for r in runs)
+    ens = sim.PicEnsemble(items, autotune=True)
+    e0 = [run.energy().total for run in ens.runs]
+    if args.warmup > 0:
+        ens.step(args.warmup)
+    for run in ens.runs:
+        run.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos, _ = ens.step(args.steps)
+    torch.cuda.synchronize()
+    t_ens = time.perf_counter() - t0
+    clk = sampler.stop()
+    profs = [run.profile(False) for run in ens.runs]
+    # the same runs one after another (each on its own stream, pic_step)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for run in ens.runs:
+        run.step(1)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    drift = max(abs(run.energy().total - a) / a for run, a in zip(ens.runs, e0))
+    iters = sum(i.total_iterations for i in infos) / max(sum(i.steps_done for i in infos), 1)
+    flops = sum(p.particle_pushes * FLOPS_PER_PARTICLE + p.push_pieces * FLOPS_PER_PUSH_PIECE +
+                p.scatter_pieces * FLOPS_PER_SCATTER_PIECE for p in profs)
+    tuning = sorted({tuple(t) for t in ens.tuning})
+    ens.close()
+    if rank != 0:
+        return
+    value = total * args.steps / t_ens
+    line = {
+        "metric": METRIC, "value": value * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_ens / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "runs": nruns, "particles_per_gpu": total,
+                   "meshes": sorted({r.n[0] for r in runs}), "precision": args.precision,
+                   "mean_picard_iterations": iters, "relative_energy_drift_max": drift,
+                   "timing": "host clock between device-wide synchronisations (runs on their own streams)",
+                   "autotuned_blocks_per_sm (fp64, fp32)": tuning,
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "alu", "achieved": flops / t_ens / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / t_ens / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_push (all runs, algorithmic flops over the whole timed region)"},
+        "sequential": {"value": total / t_seq, "unit": UNIT,
+                       "what": "the same runs, one pic_step each, one after another"},
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": int(sum(p.launches for p in profs)), "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload.startswith("ensemble-"):
+        run_ensemble(args, world, rank, local)
         return
     import torch
     import __graft_entry__ as ge

@@ -228,6 +228,44 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
  * may exceed cap), or -1 for a NULL context. */
 int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32);
 
+/* Choose the launch grids of the particle kernels for this context by measurement: the
+ * FP64 push (blocks per SM in {2, 4, 8, 16}; default 8) and, for PIC_MIXED, the FP32 chunk
+ * push ({4, 8, 16}; default 16), each timed over two launches on the context's stream from
+ * one Algorithm 1 iteration body at the current state (scratch buffers only; the committed
+ * state is unchanged).  Results are cached per process by mesh, particle count (in buckets
+ * of 16384) and precision, so further contexts of the same shape reuse them without timing.
+ * The chosen values are returned through the non-NULL pointers. */
+pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push32_blocks_per_sm);
+
+/* ---- Ensembles of independent runs -------------------------------------------------------
+ *
+ * Many small runs do not fill the GPU one at a time.  An ensemble holds `nruns` contexts,
+ * each created by pic_init from cfgs[i] and particles[i] on a stream of its own that the
+ * ensemble creates (non-blocking), with device memory from `alloc` (may be NULL: cudaMalloc).
+ * The runs may differ in mesh, particle count and every other setting.  No data is shared
+ * between runs; each run computes exactly what pic_step would compute for it alone. */
+typedef struct pic_ensemble pic_ensemble;
+
+/* PIC_ERR_ARG for nruns < 1 or NULL arrays; otherwise the first failing pic_init's status
+ * (nothing is kept then). */
+pic_status pic_ensemble_init(int32_t nruns, const pic_config* cfgs, const pic_particles* particles,
+                             const pic_allocator* alloc, pic_ensemble** out);
+
+/* Advance every run by nsteps time steps.  The runs' Picard iterations interleave: the host
+ * polls the runs' streams and queues a run's next iteration as soon as its previous one has
+ * completed, so the runs' kernels overlap on the GPU.  A run that fails (any pic_step error)
+ * stops at its last committed step while the others continue.  infos[i] / statuses[i]
+ * (either may be NULL) receive each run's pic_step-style summary and final status.  Returns
+ * PIC_OK, or the status of the lowest-numbered failed run (reason: pic_ensemble_last_error). */
+pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps, pic_step_info* infos, pic_status* statuses);
+
+/* Number of runs (-1 for NULL); run i as a context for every other call of this header
+ * (pic_energy, pic_get_state, ...; not pic_destroy: the ensemble owns it), NULL if out of range. */
+int32_t pic_ensemble_size(const pic_ensemble* e);
+pic_ctx* pic_ensemble_run(pic_ensemble* e, int32_t i);
+const char* pic_ensemble_last_error(const pic_ensemble* e);
+void pic_ensemble_destroy(pic_ensemble* e);
+
 /* Largest mesh (nodes) accepted by pic_cn_update_static. */
 #define PIC_STATIC_MAX_CELLS 32768
 

@@ -31,7 +31,8 @@ PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
             "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile", "pic_residual_history",
-            "pic_cn_update_static", "pic_last_error", "pic_destroy"]
+            "pic_cn_update_static", "pic_last_error", "pic_destroy", "pic_autotune", "pic_ensemble_init", "pic_ensemble_step",
+            "pic_ensemble_size", "pic_ensemble_run", "pic_ensemble_last_error", "pic_ensemble_destroy"]
 
 
 class PicConfig(C.Structure):
@@ -179,8 +180,20 @@ def lib():
     L.pic_last_error.restype = C.c_char_p
     L.pic_destroy.argtypes = [C.c_void_p]
     L.pic_destroy.restype = None
+    L.pic_autotune.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32)]
+    L.pic_ensemble_init.argtypes = [C.c_int32, P(PicConfig), P(PicParticles), P(PicAllocator), P(C.c_void_p)]
+    L.pic_ensemble_step.argtypes = [C.c_void_p, C.c_int32, P(PicStepInfo), P(C.c_int)]
+    L.pic_ensemble_size.argtypes = [C.c_void_p]
+    L.pic_ensemble_size.restype = C.c_int32
+    L.pic_ensemble_run.argtypes = [C.c_void_p, C.c_int32]
+    L.pic_ensemble_run.restype = C.c_void_p
+    L.pic_ensemble_last_error.argtypes = [C.c_void_p]
+    L.pic_ensemble_last_error.restype = C.c_char_p
+    L.pic_ensemble_destroy.argtypes = [C.c_void_p]
+    L.pic_ensemble_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("pic_last_error", "pic_destroy"):
+        if name not in ("pic_last_error", "pic_destroy", "pic_ensemble_size", "pic_ensemble_run",
+                        "pic_ensemble_last_error", "pic_ensemble_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

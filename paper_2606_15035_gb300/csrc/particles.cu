@@ -807,7 +807,7 @@ int local_blocks(const Ctx& c) { return std::max(1, std::min(particle_blocks(c),
 
 int particle_blocks(const Ctx& c) {
     int64_t b = (c.np + THREADS - 1) / THREADS;
-    int64_t cap = (int64_t)c.sms * 8;
+    int64_t cap = (int64_t)c.sms * c.push_bps;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;

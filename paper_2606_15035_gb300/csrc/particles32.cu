@@ -722,7 +722,7 @@ void launch_to32(Ctx& c) {
 
 int push32_blocks(const Ctx& c) {
     const int64_t chunks = (c.np + CHUNK32 - 1) / CHUNK32;
-    const int64_t cap = std::min<int64_t>((int64_t)c.sms * 16, MAX_BLOCKS);
+    const int64_t cap = std::min<int64_t>((int64_t)c.sms * c.push32_bps, MAX_BLOCKS);
     return (int)std::max<int64_t>(1, std::min(chunks, cap));
 }
 

@@ -7,8 +7,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <tuple>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -152,10 +156,15 @@ void prof_resolve(Ctx& c) {
 }
 
 // Copy results + status to the host and wait.
-pic_status sync_results(pic_ctx* ctx, const char* where) {
-    Ctx& c = ctx->c;
+// Queue the copy of the result slots and the status word to the pinned host buffers.
+void queue_results(Ctx& c) {
     cudaMemcpyAsync(c.host_results, c.results, sizeof(double) * NSLOT, cudaMemcpyDeviceToHost, c.stream);
     cudaMemcpyAsync(c.host_status, c.dev_status, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+}
+
+// Wait for the stream, then turn CUDA errors and device status bits into a status.
+pic_status wait_results(pic_ctx* ctx, const char* where) {
+    Ctx& c = ctx->c;
     cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
     if (c.prof) prof_resolve(c);
@@ -170,6 +179,11 @@ pic_status sync_results(pic_ctx* ctx, const char* where) {
     if (st & DEV_ERR_TILE)
         return fail(ctx, PIC_ERR_INTERNAL, std::string(where) + ": an orbit left the mesh tile of its block");
     return PIC_OK;
+}
+
+pic_status sync_results(pic_ctx* ctx, const char* where) {
+    queue_results(ctx->c);
+    return wait_results(ctx, where);
 }
 
 pic_status validate(const pic_config* cfg) {
@@ -335,96 +349,64 @@ void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev) {
     launch_backsub_table(c, false);
 }
 
-// One time step.  On failure nothing of the committed state (F0, W0, rho0, xi, v, P, vprev)
-// has changed except the particle order, which get_state undoes.
-pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
-    Ctx& c = ctx->c;
+// ---- one time step as a sequence of issue / finish phases --------------------------------
+//
+// step_begin queues the start of a step; then, until the iteration loop ends, iter_issue
+// queues one Algorithm 1 iteration and iter_finish (after the stream has been waited for)
+// evaluates its residuals; final_issue queues the final sweep and final_finish commits.
+// A single context runs the phases back to back (run_step); an ensemble interleaves them
+// over its runs so that their kernels overlap on the GPU.
+
+void step_begin(Ctx& c) {
+    StepRun& r = c.run;
     const int64_t N = c.m.ncell, np = c.np;
-    const bool diag = c.cfg.diagnostics != 0;
+    r = StepRun{};
     if (np > 0 && c.cfg.sort_every > 0 && c.steps % c.cfg.sort_every == 0) {
         ProfScope ps(c, PH_SORT);
         launch_sort(c);
     }
-    if (diag) queue_energy(c);
+    if (c.cfg.diagnostics) queue_energy(c);
     launch_rhs0(c);
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
     if (np > 0) cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // sliding marks live one step
-    int cur = 0, prev = 1, next = 2;
     c.hist_ev.clear();
     c.hist_eJ.clear();
     c.hist_fp32.clear();
     // PIC_MIXED: the iterations run in FP32 until they reach mixed_tol32 (or stop improving),
     // then in FP64 from the FP32 iterate.
-    bool fp32 = c.cfg.precision == PIC_MIXED && np > 0;
-    int p32 = 0;
-    double e_v32_prev = INFINITY;
-    cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
+    r.fp32 = c.cfg.precision == PIC_MIXED && np > 0;
+    cudaMemsetAsync(c.J[r.cur], 0, sizeof(double) * 3 * N, c.stream);
     {
         ProfScope ps(c, PH_SCATTER);
-        if (fp32) {
+        if (r.fp32) {
             launch_to32(c);
-            launch_scatter32(c, c.J[cur]);
+            launch_scatter32(c, c.J[r.cur]);
         } else {
-            launch_first_scatter(c, c.J[cur], nullptr);
+            launch_first_scatter(c, c.J[r.cur], nullptr);
         }
     }
     launch_finalize(c, S_JSCALE, 1, particle_blocks(c), false);
-    bool converged = false;
-    double e_v = 0.0, e_J = 0.0, jscale = 0.0;
-    int p = 0;
-    for (p = 0; p <= c.cfg.picard_max; ++p) {
-        if (fp32) {
-            mesh_phase(c, c.J[cur], p > 0 ? c.J[prev] : nullptr);
-            launch_table32(c);
-            cudaMemsetAsync(c.J[next], 0, sizeof(double) * 3 * N, c.stream);
-            {
-                ProfScope ps(c, PH_PUSH32);
-                launch_push32(c, c.J[next]);
-            }
-            launch_finalize(c, S_EV_NUM, 2, push32_blocks(c), false);
-            launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
-            pic_status s = sync_results(ctx, "pic_step (fp32)");
-            if (s != PIC_OK) return s;
-            const double* r = c.host_results;
-            if (p == 0) jscale = std::sqrt((double)N) * std::fabs(c.q) * r[S_JSCALE] / c.volume;
-            e_v = r[S_EV_DEN] > 0.0 ? std::sqrt(r[S_EV_NUM] / r[S_EV_DEN]) : 0.0;
-            {
-                double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
-                e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
-            }
-            c.hist_ev.push_back(e_v);
-            c.hist_eJ.push_back(e_J);
-            c.hist_fp32.push_back(1);
-            if (!std::isfinite(e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
-            ++p32;
-            // e_J of iteration p measures the change that iteration p - 1 made to v, so e_v alone
-            // says that the FP32 iterate has reached the FP32 noise floor
-            const bool reached = e_v <= c.cfg.mixed_tol32;
-            const bool stalled = p32 > 1 && e_v > 0.5 * e_v32_prev;
-            e_v32_prev = e_v;
-            std::swap(c.vit32, c.vnew32);
-            int old_prev = prev;
-            prev = cur;
-            cur = next;
-            next = old_prev;
-            if (reached || stalled || p32 >= c.cfg.mixed_max32) {
-                // continue in FP64 from the FP32 iterate; its current is recomputed in FP64 (the
-                // fixed-point rounding of the FP32 current would cost one more FP64 iteration)
-                launch_from32(c, c.vit32, c.vnew);   // vnew is free until the next push
-                cudaMemsetAsync(c.J[cur], 0, sizeof(double) * 3 * N, c.stream);
-                {
-                    ProfScope ps(c, PH_SCATTER);
-                    launch_first_scatter(c, c.J[cur], c.vnew);   // also copies the iterate into vit
-                }
-                fp32 = false;
-            }
-            continue;
+}
+
+// Queue iteration r.p and the copy of its residual sums.
+void iter_issue(Ctx& c) {
+    StepRun& r = c.run;
+    const int64_t N = c.m.ncell;
+    mesh_phase(c, c.J[r.cur], r.p > 0 ? c.J[r.prev] : nullptr);
+    if (r.fp32) {
+        launch_table32(c);
+        cudaMemsetAsync(c.J[r.next], 0, sizeof(double) * 3 * N, c.stream);
+        {
+            ProfScope ps(c, PH_PUSH32);
+            launch_push32(c, c.J[r.next]);
         }
-        mesh_phase(c, c.J[cur], p > 0 ? c.J[prev] : nullptr);
-        cudaMemsetAsync(c.J[next], 0, sizeof(double) * 3 * N, c.stream);
+        launch_finalize(c, S_EV_NUM, 2, push32_blocks(c), false);
+        launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
+    } else {
+        cudaMemsetAsync(c.J[r.next], 0, sizeof(double) * 3 * N, c.stream);
         {
             ProfScope ps(c, PH_PUSH);
-            launch_push(c, c.vit, c.vnew, c.J[next], false, false);
+            launch_push(c, c.vit, c.vnew, c.J[r.next], false, false);
         }
         launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
         if (c.cfg.picard_accel) launch_finalize(c, S_EVL_NUM, 2, local_blocks(c), false);
@@ -432,59 +414,110 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
         if (c.prof) launch_finalize(c, S_PIECES_PUSH, 2, particle_blocks(c), false);
         c.last_v = c.vit;
         c.last_g = c.vnew;
-        pic_status s = sync_results(ctx, "pic_step");
-        if (s != PIC_OK) return s;
-        const double* r = c.host_results;
-        if (c.prof) {
-            c.prof_acc.push_pieces += (int64_t)r[S_PIECES_PUSH];
-            c.prof_acc.scatter_pieces += (int64_t)r[S_PIECES_SCATTER];
-        }
-        if (p == 0) jscale = std::sqrt((double)N) * std::fabs(c.q) * r[S_JSCALE] / c.volume;
-        {
-            double num = r[S_EV_NUM], den = r[S_EV_DEN];
-            if (c.cfg.picard_accel) {
-                num += r[S_EVL_NUM];
-                den += r[S_EVL_DEN];
+    }
+    queue_results(c);
+}
+
+// After iter_issue's work has completed: residuals, convergence, buffer rotation.  Sets
+// r.iterating = false when the loop is over (converged, or p_max reached).
+pic_status iter_finish(pic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    StepRun& r = c.run;
+    const int64_t N = c.m.ncell;
+    const double* h = c.host_results;
+    if (r.p == 0) r.jscale = std::sqrt((double)N) * std::fabs(c.q) * h[S_JSCALE] / c.volume;
+    {
+        double num = std::sqrt(h[S_EJ_NUM]), den = std::sqrt(h[S_EJ_DEN]) + r.jscale;
+        r.e_J = r.p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
+    }
+    if (r.fp32) {
+        r.e_v = h[S_EV_DEN] > 0.0 ? std::sqrt(h[S_EV_NUM] / h[S_EV_DEN]) : 0.0;
+        c.hist_ev.push_back(r.e_v);
+        c.hist_eJ.push_back(r.e_J);
+        c.hist_fp32.push_back(1);
+        if (!std::isfinite(r.e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
+        ++r.p32;
+        // e_J of iteration p measures the change that iteration p - 1 made to v, so e_v alone
+        // says that the FP32 iterate has reached the FP32 noise floor
+        const bool reached = r.e_v <= c.cfg.mixed_tol32;
+        const bool stalled = r.p32 > 1 && r.e_v > 0.5 * r.e_v32_prev;
+        r.e_v32_prev = r.e_v;
+        std::swap(c.vit32, c.vnew32);
+        r.rotate();
+        if (reached || stalled || r.p32 >= c.cfg.mixed_max32) {
+            // continue in FP64 from the FP32 iterate; its current is recomputed in FP64 (the
+            // fixed-point rounding of the FP32 current would cost one more FP64 iteration)
+            launch_from32(c, c.vit32, c.vnew);   // vnew is free until the next push
+            cudaMemsetAsync(c.J[r.cur], 0, sizeof(double) * 3 * N, c.stream);
+            {
+                ProfScope ps(c, PH_SCATTER);
+                launch_first_scatter(c, c.J[r.cur], c.vnew);   // also copies the iterate into vit
             }
-            e_v = den > 0.0 ? std::sqrt(num / den) : 0.0;
+            r.fp32 = false;
         }
-        {
-            double num = std::sqrt(r[S_EJ_NUM]), den = std::sqrt(r[S_EJ_DEN]) + jscale;
-            e_J = p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
+    } else {
+        if (c.prof) {
+            c.prof_acc.push_pieces += (int64_t)h[S_PIECES_PUSH];
+            c.prof_acc.scatter_pieces += (int64_t)h[S_PIECES_SCATTER];
         }
-        c.hist_ev.push_back(e_v);
-        c.hist_eJ.push_back(e_J);
+        double num = h[S_EV_NUM], den = h[S_EV_DEN];
+        if (c.cfg.picard_accel) {
+            num += h[S_EVL_NUM];
+            den += h[S_EVL_DEN];
+        }
+        r.e_v = den > 0.0 ? std::sqrt(num / den) : 0.0;
+        c.hist_ev.push_back(r.e_v);
+        c.hist_eJ.push_back(r.e_J);
         c.hist_fp32.push_back(0);
-        if (!std::isfinite(e_v) || (p > 0 && !std::isfinite(e_J)))
+        if (!std::isfinite(r.e_v) || (r.p > 0 && !std::isfinite(r.e_J)))
             return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
-        if (e_v <= c.cfg.picard_tol && e_J <= c.cfg.picard_tol) {
-            converged = true;
-            break;
+        if (r.e_v <= c.cfg.picard_tol && r.e_J <= c.cfg.picard_tol) {
+            r.converged = true;
+            r.iterating = false;
+            return PIC_OK;
         }
-        if (p == c.cfg.picard_max) break;
+        if (r.p == c.cfg.picard_max) {
+            r.iterating = false;
+            return PIC_OK;
+        }
         std::swap(c.vit, c.vnew);
-        int old_prev = prev;
-        prev = cur;
-        cur = next;
-        next = old_prev;
+        r.rotate();
     }
+    if (r.p == c.cfg.picard_max) {   // the last iteration ran in FP32
+        r.iterating = false;
+        return PIC_OK;
+    }
+    ++r.p;
+    return PIC_OK;
+}
+
+// The loop is over: record the step info; refuse an unconverged step unless accepted.
+pic_status iter_close(pic_ctx* ctx, pic_step_info* last) {
+    Ctx& c = ctx->c;
+    const StepRun& r = c.run;
     if (last) {
-        last->iterations = std::min(p, c.cfg.picard_max) + 1;
-        last->iterations_fp32 = p32;
-        last->converged = converged ? 1 : 0;
-        last->e_v = e_v;
-        last->e_J = e_J;
+        last->iterations = std::min(r.p, c.cfg.picard_max) + 1;
+        last->iterations_fp32 = r.p32;
+        last->converged = r.converged ? 1 : 0;
+        last->e_v = r.e_v;
+        last->e_J = r.e_J;
     }
-    c.last_failed = !converged;
-    if (!converged && !c.cfg.accept_unconverged) {
+    c.last_failed = !r.converged;
+    if (!r.converged && !c.cfg.accept_unconverged) {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "pic_step: Picard not converged after %d iterations (e_v=%.3e, e_J=%.3e)",
-                      c.cfg.picard_max + 1, e_v, e_J);
+                      c.cfg.picard_max + 1, r.e_v, r.e_J);
         return fail(ctx, PIC_ERR_NO_CONVERGENCE, buf);
     }
-    // Final consistency sweep (§5.4): orbit of v^{n+1,p+1}, whose current is in J[next].
+    return PIC_OK;
+}
+
+// Final consistency sweep (§5.4): orbit of v^{n+1,p+1}, whose current is in J[next].
+void final_issue(Ctx& c) {
+    const StepRun& r = c.run;
+    const bool diag = c.cfg.diagnostics != 0;
     std::swap(c.vit, c.vnew);
-    double* Jfin = c.J[next];
+    double* Jfin = c.J[r.next];
     mesh_phase(c, Jfin, nullptr);
     {
         ProfScope ps(c, PH_COMMIT);
@@ -501,8 +534,13 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
         launch_finalize(c, S_R_SQ, 1, mesh_blocks(c), false);
         launch_finalize(c, S_CONT_MAX, 1, mesh_blocks(c), true);
     }
-    pic_status s = sync_results(ctx, "pic_step final sweep");
-    if (s != PIC_OK) return s;
+    queue_results(c);
+}
+
+// After final_issue's work has completed: commit level n+1 and the diagnostics.
+void final_finish(Ctx& c) {
+    const StepRun& r = c.run;
+    const int64_t N = c.m.ncell, np = c.np;
     // commit: level n+1 becomes level n; v^{n-1} <- v^n
     std::swap(c.F0, c.F1);
     std::swap(c.W0, c.W1);
@@ -512,32 +550,51 @@ pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
     std::swap(c.vprev, c.v);
     std::swap(c.v, c.vnew);
     c.steps += 1;
-    if (diag) {
-        const double* r = c.host_results;
+    if (c.cfg.diagnostics) {
+        const double* h = c.host_results;
         pic_diag_t& d = c.diag;
         const double dt = c.cfg.dt;
-        d.K0 = r[S_K];
-        d.W0 = r[S_W0];
-        d.K1 = r[S_K1];
-        d.W1 = r[S_W];
-        d.particle_work = r[S_PWORK];
-        d.mesh_work = r[S_MWORK];
+        d.K0 = h[S_K];
+        d.W0 = h[S_W0];
+        d.K1 = h[S_K1];
+        d.W1 = h[S_W];
+        d.particle_work = h[S_PWORK];
+        d.mesh_work = h[S_MWORK];
         d.R_field = d.W1 - d.W0 + dt * d.mesh_work;
         d.R_particle = d.K1 - d.K0 - dt * d.particle_work;
         d.R_total = (d.K1 + d.W1) - (d.K0 + d.W0);
-        d.RA_max = r[S_RA_MAX];
-        d.RA_rms = np > 0 ? std::sqrt(r[S_RA_SQ] / (3.0 * np)) : 0.0;
-        d.partition_max = r[S_PU_MAX];
-        d.gauge_max = r[S_G_MAX];
-        d.gauge_rms = std::sqrt(r[S_G_SQ] / (double)N);
-        d.gauss_max = r[S_R_MAX];
-        d.gauss_rms = std::sqrt(r[S_R_SQ] / (double)N);
-        d.continuity_max = r[S_CONT_MAX];
-        d.picard_iterations = std::min(p, c.cfg.picard_max) + 1;
-        d.e_v = e_v;
-        d.e_J = e_J;
+        d.RA_max = h[S_RA_MAX];
+        d.RA_rms = np > 0 ? std::sqrt(h[S_RA_SQ] / (3.0 * np)) : 0.0;
+        d.partition_max = h[S_PU_MAX];
+        d.gauge_max = h[S_G_MAX];
+        d.gauge_rms = std::sqrt(h[S_G_SQ] / (double)N);
+        d.gauss_max = h[S_R_MAX];
+        d.gauss_rms = std::sqrt(h[S_R_SQ] / (double)N);
+        d.continuity_max = h[S_CONT_MAX];
+        d.picard_iterations = std::min(r.p, c.cfg.picard_max) + 1;
+        d.e_v = r.e_v;
+        d.e_J = r.e_J;
         c.have_diag = true;
     }
+}
+
+// One time step.  On failure nothing of the committed state (F0, W0, rho0, xi, v, P, vprev)
+// has changed except the particle order, which get_state undoes.
+pic_status run_step(pic_ctx* ctx, pic_step_info* last) {
+    Ctx& c = ctx->c;
+    step_begin(c);
+    while (c.run.iterating) {
+        iter_issue(c);
+        pic_status s = wait_results(ctx, c.run.fp32 ? "pic_step (fp32)" : "pic_step");
+        if (s == PIC_OK) s = iter_finish(ctx);
+        if (s != PIC_OK) return s;
+    }
+    pic_status s = iter_close(ctx, last);
+    if (s != PIC_OK) return s;
+    final_issue(c);
+    s = wait_results(ctx, "pic_step final sweep");
+    if (s != PIC_OK) return s;
+    final_finish(c);
     return PIC_OK;
 }
 
@@ -834,6 +891,247 @@ int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, doubl
         if (fp32) fp32[k] = c.hist_fp32[k];
     }
     return n;
+}
+
+// ---- autotuning of the particle-kernel grids ---------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+struct TuneKey {
+    int n[3];
+    int64_t np_bucket;
+    int precision;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n[0], n[1], n[2], np_bucket, precision) <
+               std::tie(o.n[0], o.n[1], o.n[2], o.np_bucket, o.precision);
+    }
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // -> (push_bps, push32_bps)
+
+// Mean duration (ms) of `reps` launches queued by `launch`, after one untimed launch.
+template <typename F>
+float time_launches(Ctx& c, int reps, F&& launch) {
+    launch();
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    cudaEventRecord(a, c.stream);
+    for (int k = 0; k < reps; ++k) launch();
+    cudaEventRecord(b, c.stream);
+    cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    c.ev_pool.push_back(a);
+    c.ev_pool.push_back(b);
+    return ms / reps;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push32_blocks_per_sm) {
+    if (!ctx) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    c.err.clear();
+    const TuneKey key{{c.m.n[0], c.m.n[1], c.m.n[2]}, c.np >> 14, c.cfg.precision};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c.push_bps = it->second.first;
+            c.push32_bps = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached && c.np > 0) {
+        // One Algorithm 1 iteration body from the extrapolated guess sets up the mesh table;
+        // everything written is scratch (iterates, next current, creeping list), nothing of
+        // the committed state changes.
+        const int64_t N = c.m.ncell;
+        launch_rhs0(c);
+        cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
+        cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
+        launch_first_scatter(c, c.J[0], nullptr);
+        mesh_phase(c, c.J[0], nullptr);
+        const int cand[4] = {2, 4, 8, 16};
+        float best = INFINITY;
+        int best_bps = c.push_bps;
+        for (int bps : cand) {
+            c.push_bps = bps;
+            const float ms = time_launches(c, 2, [&] { launch_push(c, c.vit, c.vnew, c.J[1], false, false); });
+            if (ms < best) {
+                best = ms;
+                best_bps = bps;
+            }
+        }
+        c.push_bps = best_bps;
+        if (c.cfg.precision == PIC_MIXED) {
+            launch_to32(c);
+            launch_table32(c);
+            const int cand32[3] = {4, 8, 16};
+            float best32 = INFINITY;
+            int best32_bps = c.push32_bps;
+            for (int bps : cand32) {
+                c.push32_bps = bps;
+                const float ms = time_launches(c, 2, [&] {
+                    cudaMemsetAsync(c.J[1], 0, sizeof(double) * 3 * N, c.stream);
+                    launch_push32(c, c.J[1]);
+                });
+                if (ms < best32) {
+                    best32 = ms;
+                    best32_bps = bps;
+                }
+            }
+            c.push32_bps = best32_bps;
+        }
+        pic_status s = sync_results(ctx, "pic_autotune");
+        if (s != PIC_OK) return s;
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = {c.push_bps, c.push32_bps};
+    }
+    if (push_blocks_per_sm) *push_blocks_per_sm = c.push_bps;
+    if (push32_blocks_per_sm) *push32_blocks_per_sm = c.push32_bps;
+    return check_cuda(ctx, "pic_autotune");
+}
+
+// ---- ensembles -----------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct pic_ensemble {
+    std::vector<pic_ctx*> runs;
+    std::vector<cudaStream_t> streams;
+    std::string err;
+};
+
+extern "C" {
+
+pic_status pic_ensemble_init(int32_t nruns, const pic_config* cfgs, const pic_particles* particles,
+                             const pic_allocator* alloc, pic_ensemble** out) {
+    if (!out || nruns < 1 || !cfgs || !particles) return PIC_ERR_ARG;
+    *out = nullptr;
+    pic_ensemble* e = new (std::nothrow) pic_ensemble;
+    if (!e) return PIC_ERR_OOM;
+    for (int32_t i = 0; i < nruns; ++i) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            pic_ensemble_destroy(e);
+            return PIC_ERR_CUDA;
+        }
+        e->streams.push_back(st);
+        pic_ctx* c = nullptr;
+        pic_status s = pic_init(&cfgs[i], &particles[i], alloc, (void*)st, &c);
+        if (s != PIC_OK) {
+            pic_ensemble_destroy(e);
+            return s;
+        }
+        e->runs.push_back(c);
+    }
+    *out = e;
+    return PIC_OK;
+}
+
+int32_t pic_ensemble_size(const pic_ensemble* e) { return e ? (int32_t)e->runs.size() : -1; }
+
+pic_ctx* pic_ensemble_run(pic_ensemble* e, int32_t i) {
+    if (!e || i < 0 || i >= (int32_t)e->runs.size()) return nullptr;
+    return e->runs[i];
+}
+
+pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps, pic_step_info* infos, pic_status* statuses) {
+    if (!e || nsteps < 0) return PIC_ERR_ARG;
+    const int R = (int)e->runs.size();
+    std::vector<pic_step_info> acc(R), last(R);
+    std::vector<pic_status> st(R, PIC_OK);
+    std::vector<int> pending, finals;
+    for (int k = 0; k < nsteps; ++k) {
+        pending.clear();
+        finals.clear();
+        for (int r = 0; r < R; ++r) {
+            if (st[r] != PIC_OK) continue;   // a failed run stays at its last committed step
+            Ctx& c = e->runs[r]->c;
+            c.err.clear();
+            step_begin(c);
+            iter_issue(c);
+            pending.push_back(r);
+        }
+        // Poll the runs' streams; a run whose iteration has completed is evaluated and its
+        // next iteration (or its final sweep) is queued at once, while the others compute.
+        while (!pending.empty()) {
+            bool progressed = false;
+            for (size_t j = 0; j < pending.size();) {
+                const int r = pending[j];
+                pic_ctx* ctx = e->runs[r];
+                const cudaError_t q = cudaStreamQuery(ctx->c.stream);
+                if (q == cudaErrorNotReady) {
+                    ++j;
+                    continue;
+                }
+                progressed = true;
+                pic_status s = wait_results(ctx, "pic_ensemble_step");
+                if (s == PIC_OK) s = iter_finish(ctx);
+                if (s == PIC_OK && ctx->c.run.iterating) {
+                    iter_issue(ctx->c);
+                    ++j;
+                    continue;
+                }
+                if (s == PIC_OK) s = iter_close(ctx, &last[r]);
+                if (s == PIC_OK) {
+                    final_issue(ctx->c);
+                    finals.push_back(r);
+                } else {
+                    st[r] = s;
+                }
+                pending.erase(pending.begin() + (long)j);
+            }
+            if (!progressed) std::this_thread::yield();
+        }
+        for (int r : finals) {
+            pic_ctx* ctx = e->runs[r];
+            pic_status s = wait_results(ctx, "pic_ensemble_step final sweep");
+            if (s != PIC_OK) {
+                st[r] = s;
+                continue;
+            }
+            final_finish(ctx->c);
+            acc[r].steps_done += 1;
+            acc[r].total_iterations += last[r].iterations;
+            acc[r].total_iterations_fp32 += last[r].iterations_fp32;
+        }
+    }
+    pic_status first = PIC_OK;
+    e->err.clear();
+    for (int r = 0; r < R; ++r) {
+        acc[r].iterations = last[r].iterations;
+        acc[r].iterations_fp32 = last[r].iterations_fp32;
+        acc[r].converged = last[r].converged;
+        acc[r].e_v = last[r].e_v;
+        acc[r].e_J = last[r].e_J;
+        if (infos) infos[r] = acc[r];
+        if (statuses) statuses[r] = st[r];
+        if (st[r] != PIC_OK && first == PIC_OK) {
+            first = st[r];
+            e->err = "run " + std::to_string(r) + ": " + e->runs[r]->c.err;
+        }
+    }
+    return first;
+}
+
+const char* pic_ensemble_last_error(const pic_ensemble* e) {
+    if (!e) return "null ensemble";
+    return e->err.c_str();
+}
+
+void pic_ensemble_destroy(pic_ensemble* e) {
+    if (!e) return;
+    for (pic_ctx* c : e->runs) pic_destroy(c);
+    for (cudaStream_t st : e->streams) cudaStreamDestroy(st);
+    delete e;
 }
 
 const char* pic_last_error(const pic_ctx* ctx) {

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <string>
 #include <utility>
+#include <cmath>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -57,6 +58,22 @@ struct StepParams {
     int accel;                 // particle-local solves for creeping particles
 };
 
+// Host-side state of the time step in progress (see step_begin / iter_issue / iter_finish).
+struct StepRun {
+    int cur = 0, prev = 1, next = 2;   // J buffers: current iterate, previous, next
+    bool fp32 = false;                 // the next iteration runs in FP32 (PIC_MIXED)
+    bool iterating = true;             // the Picard loop is still running
+    bool converged = false;
+    int p = 0, p32 = 0;                // iteration index, FP32 iterations done
+    double e_v = 0.0, e_J = 0.0, jscale = 0.0, e_v32_prev = INFINITY;
+    void rotate() {
+        const int old_prev = prev;
+        prev = cur;
+        cur = next;
+        next = old_prev;
+    }
+};
+
 struct Ctx {
     pic_config cfg;
     cudaStream_t stream = nullptr;
@@ -66,6 +83,8 @@ struct Ctx {
 
     MeshDims m{};
     int sms = 152;
+    int push_bps = 8;     // grid of the FP64 particle kernels: blocks per SM (pic_autotune)
+    int push32_bps = 16;  // grid of the FP32 chunk kernels: blocks per SM (pic_autotune)
     double H[3], invH[3], dV = 0, volume = 0;
     int64_t np = 0;
     double q = 0, mass = 0;
@@ -94,6 +113,7 @@ struct Ctx {
     // FP32 working set of the mixed path (allocated only for PIC_MIXED)
     std::vector<double> hist_ev, hist_eJ;   // residuals of the last step's iterations
     std::vector<int32_t> hist_fp32;
+    StepRun run;
     int64_t np32 = 0;   // component stride of the FP32 arrays: np rounded up to 256 entries
     int32_t* cell32 = nullptr;
     float *off32 = nullptr, *v32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;   // iterates: increments

@@ -222,12 +222,26 @@ class PicSim:
         self.n = tuple(cfg.n)
         self.ncell = self.n[0] * self.n[1] * self.n[2]
         self.np = int(np.shape(x)[0])
+        self._owned = True
         self.ctx, self._alloc, self._keep = pic_init(cfg, x, v, q, m, stream)
 
+    @classmethod
+    def _view(cls, ctx, cfg: PicConfig, npart: int, owner):
+        """A context owned by someone else (an ensemble run); close() does not destroy it."""
+        self = cls.__new__(cls)
+        self.cfg = cfg
+        self.n = tuple(cfg.n)
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.np = int(npart)
+        self._owned = False
+        self._owner = owner
+        self.ctx = C.c_void_p(ctx)
+        return self
+
     def close(self):
-        if self.ctx:
+        if self.ctx and self._owned:
             pic_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):
         try:
@@ -252,6 +266,12 @@ class PicSim:
 
     def residual_history(self):
         return pic_residual_history(self.ctx)
+
+    def autotune(self):
+        """Measure and set the particle-kernel grids (blocks per SM): returns (fp64, fp32)."""
+        a, b = C.c_int32(), C.c_int32()
+        _check(_lib.lib().pic_autotune(self.ctx, C.byref(a), C.byref(b)), self.ctx)
+        return a.value, b.value
 
     def diagnostics(self) -> PicDiag:
         return pic_diagnostics(self.ctx)
@@ -289,3 +309,59 @@ class PicSim:
         res = {k: _mesh_to_xyz(v, self.n) for k, v in out.items()}
         res.update({k: b.reshape(3, npart).T.copy() for k, b in pt.items()})
         return res
+
+
+class PicEnsemble:
+    """Independent runs advanced together (pic_ensemble_*): runs[i] = (cfg, x, v, q, m)."""
+
+    def __init__(self, runs, autotune=False):
+        torch = _torch()
+        L = _lib.lib()
+        R = len(runs)
+        cfgs = (PicConfig * R)()
+        parts = (PicParticles * R)()
+        self._keep = []
+        self.cfgs, self.nps = [], []
+        for i, (cfg, x, v, q, m) in enumerate(runs):
+            xs, vs = soa(x), soa(v)
+            self._keep.append((xs, vs))
+            cfgs[i] = cfg
+            parts[i] = PicParticles(int(xs.shape[1]), float(q), float(m), _ptr(xs), _ptr(vs), _on_device(xs))
+            self.cfgs.append(cfg)
+            self.nps.append(int(xs.shape[1]))
+        self._alloc = _TorchAllocator(torch.cuda.current_stream().device)
+        self.ens = C.c_void_p()
+        st = L.pic_ensemble_init(R, cfgs, parts, C.byref(self._alloc.struct), C.byref(self.ens))
+        if st != _lib.PIC_OK:
+            raise PicError(st, "pic_ensemble_init failed")
+        self.runs = [PicSim._view(L.pic_ensemble_run(self.ens, i), self.cfgs[i], self.nps[i], self)
+                     for i in range(R)]
+        self.tuning = [r.autotune() for r in self.runs] if autotune else None
+
+    def __len__(self):
+        return len(self.runs)
+
+    def step(self, nsteps=1, raise_on_error=True):
+        """Advance every run; returns (infos, statuses).  With raise_on_error, a failed run
+        raises PicError (the other runs have still been advanced)."""
+        L = _lib.lib()
+        R = len(self.runs)
+        infos = (PicStepInfo * R)()
+        sts = (C.c_int * R)()
+        st = L.pic_ensemble_step(self.ens, int(nsteps), infos, sts)
+        if st != _lib.PIC_OK and raise_on_error:
+            raise PicError(st, L.pic_ensemble_last_error(self.ens).decode())
+        return list(infos), list(sts)
+
+    def close(self):
+        if self.ens:
+            for r in self.runs:
+                r.ctx = None
+            _lib.lib().pic_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

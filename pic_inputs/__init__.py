@@ -7,7 +7,10 @@ constants).  Both the CUDA path and the oracle receive the same arrays from here
 
 from .twostream import (  # noqa: F401
     WORKLOADS,
+    EnsembleRun,
     Workload,
+    ensemble_particles,
+    ensemble_runs,
     lattice_twostream,
     random_twostream,
     splitmix64_uniform,

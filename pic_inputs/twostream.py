@@ -136,3 +136,48 @@ WORKLOADS = {
 
 def workload_particles(w: Workload, run: int = 0):
     return random_twostream(w.n, w.L, w.per_beam_per_cell, w.v0, w.eps, w.vth, w.seed + run)
+
+
+# Ensemble of independent runs (seed base 1500): per run, a cubic mesh from {16, 24, 32, 48}
+# cells per side, 4..32 particles per beam per cell (8..64 per cell), beam speed uniform in
+# [0.1, 0.3], perturbation amplitude log-uniform in [1e-4, 1e-2], cold beams, run seed
+# 1500 + run.  The run parameters are draws 4 r .. 4 r + 3 of stream 1500.
+ENSEMBLE_SEED = 1500
+ENSEMBLE_GRIDS = (16, 24, 32, 48)
+
+
+@dataclass(frozen=True)
+class EnsembleRun:
+    n: tuple
+    per_beam_per_cell: int
+    v0: float
+    eps: float
+    seed: int
+    dt: float = 0.1
+    picard_tol: float = 1e-13
+
+    @property
+    def L(self):
+        side = 2.0 * np.pi / 3.0
+        return (side, side, side)
+
+    @property
+    def n_particles(self):
+        return 2 * self.per_beam_per_cell * self.n[0] * self.n[1] * self.n[2]
+
+
+def ensemble_runs(nruns=64, seed=ENSEMBLE_SEED, grids=ENSEMBLE_GRIDS, ppb=(4, 32)):
+    """The ensemble's run list (parameters only; ensemble_particles draws each run)."""
+    u = splitmix64_uniform(seed, np.arange(4 * nruns, dtype=np.uint64)).reshape(nruns, 4)
+    runs = []
+    for r in range(nruns):
+        g = grids[min(int(u[r, 0] * len(grids)), len(grids) - 1)]
+        per_beam = ppb[0] + min(int(u[r, 1] * (ppb[1] - ppb[0] + 1)), ppb[1] - ppb[0])
+        v0 = 0.1 + 0.2 * u[r, 2]
+        eps = 10.0 ** (-4.0 + 2.0 * u[r, 3])
+        runs.append(EnsembleRun((g, g, g), per_beam, float(v0), float(eps), seed + r))
+    return runs
+
+
+def ensemble_particles(run: EnsembleRun):
+    return random_twostream(run.n, run.L, run.per_beam_per_cell, run.v0, run.eps, 0.0, run.seed)

@@ -37,3 +37,15 @@ def test_deterministic_and_thermal_spread():
     assert np.abs(a[0] - c[0]).max() > 0.1
     dv = a[1][:, 1:]
     assert abs(np.std(dv) - 1e-4) < 5e-6 and abs(np.mean(dv)) < 5e-6
+
+
+def test_ensemble_runs_are_seeded_and_in_range():
+    import pic_inputs as pi
+    a, b = pi.ensemble_runs(), pi.ensemble_runs()
+    assert a == b and len(a) == 64
+    assert {r.n[0] for r in a} == {16, 24, 32, 48}
+    assert all(4 <= r.per_beam_per_cell <= 32 for r in a)
+    assert all(0.1 <= r.v0 <= 0.3 and 1e-4 <= r.eps <= 1e-2 for r in a)
+    assert len({r.seed for r in a}) == 64
+    x, v, q, m = pi.ensemble_particles(a[0])
+    assert x.shape == (a[0].n_particles, 3) and np.isclose(abs(v[:, 0]).max(), a[0].v0, rtol=0.2)
