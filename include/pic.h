@@ -87,6 +87,13 @@ typedef struct {
     double helmholtz_tol;         /* target error reduction of the CN Helmholtz solve (Chebyshev) */
     double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v <= this */
     int32_t mixed_max32;          /* PIC_MIXED: at most this many FP32 iterations per step */
+    int32_t deterministic;        /* 1: bitwise reproducible steps.  The particle sort is a stable
+                                     radix sort, the current and charge deposits are exact sums in
+                                     2 x 64-bit fixed point (integer atomics, order independent),
+                                     creeping particles are solved in index order and the launch
+                                     grids are the defaults (pic_autotune changes nothing).  The
+                                     same inputs then give the same bits, run after run and alone
+                                     or in an ensemble.  Needs |v| < 100 kappa. */
 } pic_config;
 
 /* Initial particles of one species. */
@@ -177,7 +184,7 @@ typedef struct {
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
  * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
- * at most 8 FP32 iterations. */
+ * at most 8 FP32 iterations, not deterministic. */
 pic_status pic_config_default(pic_config* cfg);
 
 /* Create a context: copies the particles to the device, sorts them by cell, deposits

@@ -57,6 +57,7 @@ class PicConfig(C.Structure):
         ("helmholtz_tol", C.c_double),
         ("mixed_tol32", C.c_double),
         ("mixed_max32", C.c_int32),
+        ("deterministic", C.c_int32),
     ]
 
 

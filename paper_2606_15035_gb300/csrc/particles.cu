@@ -4,6 +4,7 @@
 // (component c of particle i at c * np + i) and cell-sorted so that neighbouring
 // threads gather the same mesh nodes.  Mesh data for the gather come from a per-node
 // table of 12 doubles: A^n (3), A^{n+1,p} (3), grad_h phi^{n+1/2,p} (3), U^{n+1/2,p} (3).
+#include <algorithm>
 #include <cmath>
 
 #include "pic_internal.h"
@@ -57,9 +58,15 @@ __device__ __forceinline__ int scatter_closed(const StepParams& p, const double 
         segment_nodes8(sg, p.m, g);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            atomicAdd(J + g[k], w[0] * I[k]);
-            atomicAdd(J + N + g[k], w[1] * I[k]);
-            atomicAdd(J + 2 * N + g[k], w[2] * I[k]);
+            if (p.det) {
+                exact_add(p.acc, g[k], w[0] * I[k]);
+                exact_add(p.acc, N + g[k], w[1] * I[k]);
+                exact_add(p.acc, 2 * N + g[k], w[2] * I[k]);
+            } else {
+                atomicAdd(J + g[k], w[0] * I[k]);
+                atomicAdd(J + N + g[k], w[1] * I[k]);
+                atomicAdd(J + 2 * N + g[k], w[2] * I[k]);
+            }
         }
     });
 }
@@ -79,9 +86,15 @@ __device__ __forceinline__ int scatter_gauss(const StepParams& p, const double x
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 double f = wq * S[k];
-                atomicAdd(J + g[k], w[0] * f);
-                atomicAdd(J + N + g[k], w[1] * f);
-                atomicAdd(J + 2 * N + g[k], w[2] * f);
+                if (p.det) {
+                    exact_add(p.acc, g[k], w[0] * f);
+                    exact_add(p.acc, N + g[k], w[1] * f);
+                    exact_add(p.acc, 2 * N + g[k], w[2] * f);
+                } else {
+                    atomicAdd(J + g[k], w[0] * f);
+                    atomicAdd(J + N + g[k], w[1] * f);
+                    atomicAdd(J + 2 * N + g[k], w[2] * f);
+                }
             }
         }
     });
@@ -314,7 +327,10 @@ __global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, dou
         double w[8];
         point_weights8(x, p.m, g, w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) atomicAdd(rho + g[k], p.q_dV * w[k]);
+        for (int k = 0; k < 8; ++k) {
+            if (p.det) exact_add(p.acc, g[k], p.q_dV * w[k]);
+            else atomicAdd(rho + g[k], p.q_dV * w[k]);
+        }
     }
 }
 
@@ -404,6 +420,7 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
                                                   double* __restrict__ vnew, double* __restrict__ Jnext,
                                                   double* __restrict__ xi_out, double* __restrict__ P_out,
                                                   int32_t* __restrict__ creep_list, int* __restrict__ creep_count,
+                                                  uint8_t* __restrict__ creep_flag,
                                                   const uint8_t* __restrict__ slide, double* __restrict__ partials,
                                                   int* __restrict__ status) {
     __shared__ double sm[32];
@@ -439,9 +456,13 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
                 bet2[a] = p.dt * vb2 * p.invH[a];
                 wv[a] = p.q_dV * vb2;
             }
-            if (p.accel && is_creeping(x0, beta_it)) {
-                int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
-                creep_list[k] = (int32_t)i;
+            const bool creep = p.accel && is_creeping(x0, beta_it);
+            if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
+            if (creep) {
+                if (!creep_flag) {
+                    int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
+                    creep_list[k] = (int32_t)i;
+                }
             } else {
                 ev_num += dnum;
                 ev_den += dden;
@@ -517,14 +538,17 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                                                    const double* __restrict__ vit, const double* __restrict__ table,
                                                    double* __restrict__ vnew, double* __restrict__ gsave,
                                                    double* __restrict__ Jnext, const int32_t* __restrict__ creep_list,
-                                                   const int* __restrict__ creep_count, uint8_t* __restrict__ slide,
+                                                   const int* __restrict__ creep_count,
+                                                   const uint8_t* __restrict__ creep_flag, uint8_t* __restrict__ slide,
                                                    double* __restrict__ partials, int* __restrict__ status) {
     __shared__ double sm[32];
     const int64_t np = p.np;
-    const int count = *creep_count;
+    // the creeping particles: a list in arrival order, or (deterministic mode) flags in index order
+    const int64_t count = creep_flag ? np : (int64_t)*creep_count;
     double ev_num = 0.0, ev_den = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
-        const int64_t i = creep_list[k];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        if (creep_flag && !creep_flag[k]) continue;
+        const int64_t i = creep_flag ? k : (int64_t)creep_list[k];
         double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
         double ua[3], ga[3], ub[3], gb[3], side[3], fac[3];
         bool brk[3], secok[3];
@@ -760,6 +784,97 @@ __global__ void k_sort_scatter(StepParams p, const int32_t* __restrict__ key, co
     }
 }
 
+// ---- stable LSD radix sort of the cell keys (deterministic mode) ---------------------------
+//
+// 8-bit digits; each pass counts the digits of every tile of RS_TILE keys, scans the counts
+// in digit-major order (so tile b's keys of digit d go after those of every earlier tile),
+// and scatters each tile in index order, ranking equal digits within a warp by
+// __match_any_sync.  Every pass is stable, so the result is ordered by key and, among equal
+// keys, by the previous order: a deterministic permutation.
+
+constexpr int RS_RADIX = 256, RS_ITEMS = 8, RS_TILE = THREADS * RS_ITEMS;
+static_assert(THREADS == RS_RADIX, "one thread per digit in the scatter's bookkeeping");
+
+__global__ void k_rs_hist(const int32_t* __restrict__ key, int64_t n, int shift, int ntiles,
+                          int32_t* __restrict__ hist) {
+    __shared__ int32_t cnt[RS_RADIX];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = base + r * THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(key[i] >> shift) & (RS_RADIX - 1)], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const int32_t* __restrict__ key_in, const int32_t* __restrict__ val_in, int64_t n,
+                             int shift, int ntiles, const int32_t* __restrict__ offs, int32_t* __restrict__ key_out,
+                             int32_t* __restrict__ val_out) {
+    __shared__ int32_t run[RS_RADIX];
+    __shared__ int32_t wc[THREADS / 32][RS_RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    run[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+#pragma unroll
+    for (int v = 0; v < THREADS / 32; ++v) wc[v][tid] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = base + r * THREADS + tid;
+        const bool valid = i < n;
+        const int32_t k = valid ? key_in[i] : 0;
+        const int d = valid ? (k >> shift) & (RS_RADIX - 1) : RS_RADIX + lane;   // invalid lanes: own groups
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wc[w][d] = __popc(peers);
+        __syncthreads();
+        int pos = 0;
+        if (valid) {
+            pos = run[d] + rank;
+            for (int v = 0; v < w; ++v) pos += wc[v][d];
+        }
+        __syncthreads();
+        int add = 0;
+#pragma unroll
+        for (int v = 0; v < THREADS / 32; ++v) {
+            add += wc[v][tid];
+            wc[v][tid] = 0;
+        }
+        run[tid] += add;
+        __syncthreads();
+        if (valid) {
+            key_out[pos] = k;
+            val_out[pos] = val_in[i];
+        }
+    }
+}
+
+__global__ void k_iota(int64_t n, int32_t* __restrict__ a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+// Destination j takes particle perm[j].
+__global__ void k_sort_gather(StepParams p, const int32_t* __restrict__ perm, const double* __restrict__ xi,
+                              const double* __restrict__ v, const double* __restrict__ P,
+                              const double* __restrict__ vprev, const int64_t* __restrict__ id,
+                              double* __restrict__ xi_d, double* __restrict__ v_d, double* __restrict__ P_d,
+                              double* __restrict__ vprev_d, int64_t* __restrict__ id_d) {
+    const int64_t np = p.np;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xi_d[a * np + j] = xi[a * np + i];
+            v_d[a * np + j] = v[a * np + i];
+            P_d[a * np + j] = P[a * np + i];
+            vprev_d[a * np + j] = vprev[a * np + i];
+        }
+        id_d[j] = id[i];
+    }
+}
+
 // dst[c, id[i]] = scale_c * src[c, i]  (device order -> caller order)
 __global__ void k_unpermute(int64_t np, const int64_t* __restrict__ id, const double* __restrict__ src,
                             double* __restrict__ dst, double s0, double s1, double s2) {
@@ -798,6 +913,8 @@ StepParams make_params(const Ctx& c) {
     p.split = c.cfg.split_orbit_at_knots;
     p.nq = c.cfg.nq;
     p.accel = c.cfg.picard_accel;
+    p.det = c.cfg.deterministic;
+    p.acc = ExactAcc{c.acc_hi, c.acc_lo, c.inv_u_J, c.dev_status};
     return p;
 }
 
@@ -821,8 +938,10 @@ void launch_init_positions(Ctx& c, const double* x_dev) {
 
 void launch_point_deposit(Ctx& c) {
     StepParams p = make_params(c);
+    p.acc.inv_u = c.inv_u_rho;
     k_point_deposit<<<particle_blocks(c), THREADS, 0, c.stream>>>(p, c.xi, c.rho0);
     ++c.launches;
+    if (c.cfg.deterministic) launch_exact_finish(c, c.rho0, c.m.ncell, c.inv_u_rho);
 }
 
 void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null) {
@@ -835,16 +954,19 @@ void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null) {
         k_first_scatter<1><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.vprev, v_iter_or_null, c.vit, J, c.partials,
                                                          c.dev_status);
     ++c.launches;
+    if (c.cfg.deterministic) launch_exact_finish(c, J, 3 * c.m.ncell, c.inv_u_J);
 }
 
 void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag) {
     StepParams p = make_params(c);
     int nb = particle_blocks(c);
+    const bool det = c.cfg.deterministic && !commit;
     const bool closed = c.cfg.quadrature == PIC_QUAD_CLOSED;
     if (!commit) cudaMemsetAsync(c.creep_count, 0, sizeof(int), c.stream);
 #define PIC_PUSH(Q, C, D)                                                                                        \
     k_push<Q, C, D><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.xi_new, c.P_new, \
-                                                  c.creep_list, c.creep_count, commit ? c.slide : nullptr,    \
+                                                  c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,  \
+                                                  commit ? c.slide : nullptr,                                 \
                                                   c.partials, c.dev_status)
     if (!commit) {
         if (closed) PIC_PUSH(0, false, false);
@@ -862,14 +984,15 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
         int lb = local_blocks(c);
         if (closed)
             k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
-                                                     c.creep_list, c.creep_count, c.slide, c.partials,
-                                                     c.dev_status);
+                                                     c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
+                                                     c.slide, c.partials, c.dev_status);
         else
             k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
-                                                     c.creep_list, c.creep_count, c.slide, c.partials,
-                                                     c.dev_status);
+                                                     c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
+                                                     c.slide, c.partials, c.dev_status);
         ++c.launches;
     }
+    if (det && Jnext) launch_exact_finish(c, Jnext, 3 * c.m.ncell, c.inv_u_J);
 }
 
 void launch_kinetic(Ctx& c) {
@@ -878,7 +1001,69 @@ void launch_kinetic(Ctx& c) {
     ++c.launches;
 }
 
+// out[i] = (hi[i] 2^40 + lo[i]) u, then hi[i] = lo[i] = 0 for the next deposit (the
+// deterministic mode's exact accumulators; see ExactAcc).
+__global__ void k_exact_finish(int64_t n, long long* __restrict__ hi, long long* __restrict__ lo, double u,
+                               double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        out[i] = ((double)hi[i] * 0x1p40 + (double)lo[i]) * u;
+        hi[i] = 0;
+        lo[i] = 0;
+    }
+}
+
+void launch_exact_finish(Ctx& c, double* out, int64_t n, double inv_u) {
+    int64_t nb = (n + THREADS - 1) / THREADS;
+    if (nb > (int64_t)c.sms * 8) nb = (int64_t)c.sms * 8;
+    if (nb < 1) nb = 1;
+    k_exact_finish<<<(int)nb, THREADS, 0, c.stream>>>(n, c.acc_hi, c.acc_lo, 1.0 / inv_u, out);
+    ++c.launches;
+}
+
+int radix_tiles(int64_t np) { return (int)std::max<int64_t>(1, (np + RS_TILE - 1) / RS_TILE); }
+
+// Stable radix sort of the cell keys; the particle arrays are then gathered in that order.
+void launch_sort_stable(Ctx& c) {
+    StepParams p = make_params(c);
+    const int64_t N = c.m.ncell, np = c.np;
+    const int nb = particle_blocks(c);
+    cudaMemsetAsync(c.count, 0, sizeof(int32_t) * N, c.stream);
+    k_sort_keys<<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.rs_key[0], c.count);
+    k_iota<<<nb, THREADS, 0, c.stream>>>(np, c.rs_val[0]);
+    c.launches += 2;
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < N) ++bits;
+    const int passes = std::max(1, (bits + 7) / 8);
+    const int ntiles = radix_tiles(np);
+    const int64_t nh = (int64_t)RS_RADIX * ntiles;
+    const int nsb = (int)((nh + 1023) / 1024);
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<ntiles, THREADS, 0, c.stream>>>(c.rs_key[cur], np, shift, ntiles, c.rs_hist);
+        k_scan_local<<<nsb, 1024, 0, c.stream>>>(c.rs_hist, c.rs_offs, c.rs_scan_tmp, nh);
+        k_scan_totals<<<1, 1024, 0, c.stream>>>(c.rs_scan_tmp, nsb);
+        k_scan_add<<<nsb, 1024, 0, c.stream>>>(c.rs_offs, c.rs_scan_tmp, nh);
+        k_rs_scatter<<<ntiles, THREADS, 0, c.stream>>>(c.rs_key[cur], c.rs_val[cur], np, shift, ntiles, c.rs_offs,
+                                                        c.rs_key[cur ^ 1], c.rs_val[cur ^ 1]);
+        c.launches += 5;
+        cur ^= 1;
+    }
+    k_sort_gather<<<nb, THREADS, 0, c.stream>>>(p, c.rs_val[cur], c.xi, c.v, c.P, c.vprev, c.id, c.xi_new, c.vnew,
+                                                c.P_new, c.vit, c.id_tmp);
+    ++c.launches;
+    std::swap(c.xi, c.xi_new);
+    std::swap(c.v, c.vnew);
+    std::swap(c.P, c.P_new);
+    std::swap(c.vprev, c.vit);
+    std::swap(c.id, c.id_tmp);
+}
+
 void launch_sort(Ctx& c) {
+    if (c.cfg.deterministic) {
+        launch_sort_stable(c);
+        return;
+    }
     StepParams p = make_params(c);
     const int64_t N = c.m.ncell;
     int nb = particle_blocks(c);

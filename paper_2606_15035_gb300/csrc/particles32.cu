@@ -41,6 +41,8 @@ struct Params32 {
     float dt, q, inv_mass, q_dV;
     int64_t np;
     int64_t stride;   // component stride of the FP32 particle arrays (a multiple of CHUNK32)
+    int det;          // deterministic mode: FP64 deposits go to acc (exact, order independent)
+    ExactAcc acc;
 };
 
 template <typename T>
@@ -176,6 +178,8 @@ struct MeshView {
     int* jt;             // TILED: 3 x TILE_CAP current in fixed point (units of 1 / jscale[a])
     float jscale[3];     // TILED: per component, a power of two with |contribution| * jscale < 2^21
     double* J;           // !TILED: FP64 current, 3 x N
+    ExactAcc acc;        // !TILED, deterministic mode: exact accumulator of J
+    int det;
     Box box;
     MeshDims m;
     int* status;
@@ -205,6 +209,10 @@ struct MeshView {
             atomicAdd(jt + g[k], to_fixed(w0, jscale[0]));
             atomicAdd(jt + TILE_CAP + g[k], to_fixed(w1, jscale[1]));
             atomicAdd(jt + 2 * TILE_CAP + g[k], to_fixed(w2, jscale[2]));
+        } else if (det) {
+            exact_add(acc, gg[k], (double)w0);
+            exact_add(acc, m.ncell + gg[k], (double)w1);
+            exact_add(acc, 2 * m.ncell + gg[k], (double)w2);
         } else {
             atomicAdd(J + gg[k], (double)w0);
             atomicAdd(J + m.ncell + gg[k], (double)w1);
@@ -348,16 +356,23 @@ __device__ __forceinline__ void zero_jtile(const Box& b, int* jt) {
 }
 
 // Add the chunk's FP32 current tile to the FP64 J (nodes that received nothing are skipped).
-__device__ __forceinline__ void flush_jtile(const Box& b, const int ref[3], const MeshDims& m, const int* jt,
+__device__ __forceinline__ void flush_jtile(const Params32& p, const Box& b, const int ref[3], const int* jt,
                                             const float jscale[3], double* __restrict__ J) {
+    const MeshDims& m = p.m;
     const double i0 = 1.0 / (double)jscale[0], i1 = 1.0 / (double)jscale[1], i2 = 1.0 / (double)jscale[2];
     for (int l = threadIdx.x; l < b.vol; l += blockDim.x) {
         const int j0 = jt[l], j1 = jt[TILE_CAP + l], j2 = jt[2 * TILE_CAP + l];
         if ((j0 | j1 | j2) == 0) continue;
         const int64_t g = tile_global(b, ref, m, l);
-        if (j0 != 0) atomicAdd(J + g, i0 * j0);
-        if (j1 != 0) atomicAdd(J + m.ncell + g, i1 * j1);
-        if (j2 != 0) atomicAdd(J + 2 * m.ncell + g, i2 * j2);
+        if (p.det) {
+            if (j0 != 0) exact_add(p.acc, g, i0 * j0);
+            if (j1 != 0) exact_add(p.acc, m.ncell + g, i1 * j1);
+            if (j2 != 0) exact_add(p.acc, 2 * m.ncell + g, i2 * j2);
+        } else {
+            if (j0 != 0) atomicAdd(J + g, i0 * j0);
+            if (j1 != 0) atomicAdd(J + m.ncell + g, i1 * j1);
+            if (j2 != 0) atomicAdd(J + 2 * m.ncell + g, i2 * j2);
+        }
     }
 }
 
@@ -522,13 +537,13 @@ __device__ __forceinline__ void chunk_scatter(const Params32& p, const Chunk& k,
         zero_jtile(b, jt);
         __syncthreads();
         if (k.valid) {
-            MeshView<true> mv{nullptr, jt, {js[0], js[1], js[2]}, nullptr, b, p.m, status};
+            MeshView<true> mv{nullptr, jt, {js[0], js[1], js[2]}, nullptr, p.acc, p.det, b, p.m, status};
             if (scatter32(mv, co, x0, beta, w) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
         }
         __syncthreads();
-        flush_jtile(b, k.ref, p.m, jt, js, J);
+        flush_jtile(p, b, k.ref, jt, js, J);
     } else if (k.valid) {
-        MeshView<false> mv{nullptr, nullptr, {0.f, 0.f, 0.f}, J, b, p.m, status};
+        MeshView<false> mv{nullptr, nullptr, {0.f, 0.f, 0.f}, J, p.acc, p.det, b, p.m, status};
         if (scatter32(mv, cb, x0, beta, w) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
     }
 }
@@ -642,10 +657,10 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
             float dv[3];
             int ns;
             if (tiled) {
-                MeshView<true> mv{tab, nullptr, {0.f, 0.f, 0.f}, nullptr, bx, p.m, status};
+                MeshView<true> mv{tab, nullptr, {0.f, 0.f, 0.f}, nullptr, p.acc, p.det, bx, p.m, status};
                 ns = push32(p, mv, co, x0, beta, vb, dv);
             } else {
-                MeshView<false> mv{table4, nullptr, {0.f, 0.f, 0.f}, nullptr, bx, p.m, status};
+                MeshView<false> mv{table4, nullptr, {0.f, 0.f, 0.f}, nullptr, p.acc, p.det, bx, p.m, status};
                 ns = push32(p, mv, cb, x0, beta, vb, dv);
             }
             if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
@@ -709,6 +724,8 @@ Params32 make_params32(const Ctx& c) {
     p.q_dV = (float)(c.q / c.dV);
     p.np = c.np;
     p.stride = c.np32;
+    p.det = c.cfg.deterministic;
+    p.acc = ExactAcc{c.acc_hi, c.acc_lo, c.inv_u_J, c.dev_status};
     return p;
 }
 
@@ -730,12 +747,14 @@ void launch_scatter32(Ctx& c, double* J) {
     k_scatter32<<<push32_blocks(c), CHUNK32, 0, c.stream>>>(make_params32(c), c.cell32, c.off32, c.v32, c.vit32, J,
                                                               c.dev_status);
     ++c.launches;
+    if (c.cfg.deterministic) launch_exact_finish(c, J, 3 * c.m.ncell, c.inv_u_J);
 }
 
 void launch_push32(Ctx& c, double* Jnext) {
     k_push32<<<push32_blocks(c), CHUNK32, 0, c.stream>>>(make_params32(c), c.cell32, c.off32, c.v32, c.vit32,
                                                            c.table32, c.vnew32, Jnext, c.partials, c.dev_status);
     ++c.launches;
+    if (c.cfg.deterministic) launch_exact_finish(c, Jnext, 3 * c.m.ncell, c.inv_u_J);
 }
 
 void launch_table32(Ctx& c) {

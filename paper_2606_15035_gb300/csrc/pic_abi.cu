@@ -174,6 +174,9 @@ pic_status wait_results(pic_ctx* ctx, const char* where) {
     if (st & DEV_ERR_SEGMENTS)
         return fail(ctx, PIC_ERR_SEGMENTS, std::string(where) + ": an orbit crossed more knots than supported in one step");
     if (st & DEV_ERR_NONFINITE) return fail(ctx, PIC_ERR_NONFINITE, std::string(where) + ": non-finite particle velocity");
+    if (st & DEV_ERR_RANGE)
+        return fail(ctx, PIC_ERR_NONFINITE, std::string(where) + ": a deposit beyond the exact accumulator's range "
+                                                               "(a speed above 100 kappa in deterministic mode)");
     if (st & DEV_ERR_TIMEOUT)
         return fail(ctx, PIC_ERR_TIMEOUT, std::string(where) + ": a bulk copy into shared memory did not complete");
     if (st & DEV_ERR_TILE)
@@ -282,6 +285,32 @@ pic_status allocate(pic_ctx* ctx) {
             if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
                 return fail(ctx, PIC_ERR_ARG, "the allocator returned a pointer that is not 16-byte aligned");
         ALLOC(c.table32, float, 12 * N);
+    }
+    if (c.cfg.deterministic) {
+        ALLOC(c.acc_hi, long long, 3 * N);
+        ALLOC(c.acc_lo, long long, 3 * N);
+        cudaMemsetAsync(c.acc_hi, 0, sizeof(long long) * 3 * N, c.stream);
+        cudaMemsetAsync(c.acc_lo, 0, sizeof(long long) * 3 * N, c.stream);
+        ALLOC(c.creep_flag, uint8_t, std::max<int64_t>(c.np, 1));
+        const int64_t np1 = std::max<int64_t>(c.np, 1);
+        const int64_t nh = (int64_t)256 * radix_tiles(c.np);
+        for (int k = 0; k < 2; ++k) {
+            ALLOC(c.rs_key[k], int32_t, np1);
+            ALLOC(c.rs_val[k], int32_t, np1);
+        }
+        ALLOC(c.rs_hist, int32_t, nh);
+        ALLOC(c.rs_offs, int32_t, nh);
+        ALLOC(c.rs_scan_tmp, int32_t, (nh + 1023) / 1024 + 1);
+        // scales of the exact accumulators: bounds on the sum of |deposit| into one entry,
+        // sum_i |q| |vbar_i| / dV (speeds below 100 kappa) for J and sum_i |q| / dV for rho
+        const double wq = std::max<double>((double)c.np, 1.0) * std::fabs(c.q) / c.dV;
+        auto inv_u = [](double W) {
+            int e = 0;
+            std::frexp(std::max(W, 1e-300), &e);   // W < 2^e
+            return std::ldexp(1.0, 102 - e);
+        };
+        c.inv_u_J = inv_u(wq * 100.0 * c.cfg.kappa);
+        c.inv_u_rho = inv_u(wq);
     }
     ALLOC(c.partials, double, (size_t)NSLOT * MAX_BLOCKS);
     ALLOC(c.results, double, NSLOT);
@@ -625,6 +654,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->picard_accel = 1;
     cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
+    cfg->deterministic = 0;
     cfg->helmholtz_tol = 1e-17;
     return PIC_OK;
 }
@@ -937,8 +967,8 @@ pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push
     Ctx& c = ctx->c;
     c.err.clear();
     const TuneKey key{{c.m.n[0], c.m.n[1], c.m.n[2]}, c.np >> 14, c.cfg.precision};
-    bool cached = false;
-    {
+    bool cached = c.cfg.deterministic != 0;   // deterministic mode keeps the default grids
+    if (!cached) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {

@@ -18,6 +18,7 @@ enum : int {
     DEV_ERR_NONFINITE = 2,  // a non-finite velocity or residual appeared
     DEV_ERR_TILE = 4,       // an orbit left the mesh tile computed for its block (not expected)
     DEV_ERR_TIMEOUT = 8,    // a bounded wait on an asynchronous copy gave up
+    DEV_ERR_RANGE = 16,     // a deposit beyond the exact accumulator's range (deterministic mode)
 };
 
 constexpr int MAX_SEGMENTS = 64;
@@ -287,6 +288,33 @@ __device__ __forceinline__ void point_weights8(const T xi[3], const MeshDims& m,
                 T wz = nz ? r[2] : T(1) - r[2];
                 w[nx + 2 * ny + 4 * nz] = wx * wy * wz;
             }
+}
+
+// ---- exact, order-independent accumulation (deterministic mode) --------------------------
+//
+// A deposit x is added as the integer N = round(x / u), u a power of two, split into
+// N = hi * 2^40 + lo with 0 <= lo < 2^40; hi and lo go to two 64-bit integer accumulators.
+// Integer addition is associative, so the sums do not depend on the order in which threads
+// add, and the only rounding is that of each x to a multiple of u.  u is chosen from a bound W
+// on the sum of |x| over all deposits to one entry, u = 2^(ceil(log2 W) - 102): then every
+// |hi| sum stays below 2^63 and u / |x| is ~1e-21 for a typical deposit.
+struct ExactAcc {
+    long long* hi;    // one per entry
+    long long* lo;
+    double inv_u;     // 1 / u
+    int* status;
+};
+
+__device__ __forceinline__ void exact_add(const ExactAcc& a, int64_t idx, double x) {
+    const double t = x * a.inv_u;                       // exact: scaling by a power of two
+    if (!(fabs(t) < 0x1p100)) {
+        atomicOr(a.status, DEV_ERR_RANGE);
+        return;
+    }
+    const double h = floor(t * 0x1p-40);                // exact
+    const double l = t - h * 0x1p40;                    // in [0, 2^40], exact for |t| >= 2^40
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.hi + idx), (unsigned long long)(long long)h);
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.lo + idx), (unsigned long long)llrint(l));
 }
 
 // ---- "creeping" orbits --------------------------------------------------------------------

@@ -56,6 +56,8 @@ struct StepParams {
     int split;                 // split orbits at knots
     int nq;                    // Gauss points (Gauss quadrature only)
     int accel;                 // particle-local solves for creeping particles
+    int det;                   // deterministic mode: deposits go to acc (exact, order independent)
+    ExactAcc acc;
 };
 
 // Host-side state of the time step in progress (see step_begin / iter_issue / iter_finish).
@@ -114,6 +116,13 @@ struct Ctx {
     std::vector<double> hist_ev, hist_eJ;   // residuals of the last step's iterations
     std::vector<int32_t> hist_fp32;
     StepRun run;
+    // deterministic mode: exact deposit accumulators (3 N each), their scales, creeping flags,
+    // and the radix-sort work arrays
+    long long *acc_hi = nullptr, *acc_lo = nullptr;
+    double inv_u_J = 1.0, inv_u_rho = 1.0;
+    uint8_t* creep_flag = nullptr;
+    int32_t *rs_key[2] = {nullptr, nullptr}, *rs_val[2] = {nullptr, nullptr}, *rs_hist = nullptr, *rs_offs = nullptr;
+    int32_t* rs_scan_tmp = nullptr;
     int64_t np32 = 0;   // component stride of the FP32 arrays: np rounded up to 256 entries
     int32_t* cell32 = nullptr;
     float *off32 = nullptr, *v32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;   // iterates: increments
@@ -162,6 +171,8 @@ void set_gauss_rule(int nq);
 void launch_to32(Ctx& c);
 void launch_scatter32(Ctx& c, double* J);
 void launch_push32(Ctx& c, double* Jnext);
+void launch_exact_finish(Ctx& c, double* out, int64_t n, double inv_u);   // acc -> out, acc = 0
+int radix_tiles(int64_t np);
 int push32_blocks(const Ctx& c);   // grid of the FP32 chunk kernels (partials per block)
 void launch_table32(Ctx& c);
 void launch_from32(Ctx& c, const float* a, double* b);

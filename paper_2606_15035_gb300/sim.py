@@ -36,7 +36,8 @@ def pic_config_default(**overrides) -> PicConfig:
             for a in range(3):
                 arr[a] = v[a]
         elif k == "split_orbit_at_knots" or k in ("picard_max", "quadrature", "nq", "precision", "sort_every",
-                                                  "diagnostics", "accept_unconverged", "picard_accel", "mixed_max32", "precision"):
+                                                  "diagnostics", "accept_unconverged", "picard_accel", "mixed_max32",
+                                                  "deterministic"):
             setattr(cfg, k, int(v))
         else:
             setattr(cfg, k, float(v))
