@@ -36,6 +36,30 @@ class OrbitWeights:
     T1: np.ndarray      # (np, K, 3)
 
 
+def knot_offset(order):
+    """Knot positions of the degree-r B-spline centred on the nodes, in cell units: the
+    integers for odd r and the half-integers for even r (the nodes sit at the integers)."""
+    return 0.5 if order % 2 == 0 else 0.0
+
+
+def bspline(x, r):
+    """Centred cardinal B-spline of degree r at x (support |x| < (r + 1)/2): the Cox--de Boor
+    recursion N_k(y) = [y N_{k-1}(y) + (k + 1 - y) N_{k-1}(y - 1)] / k, N_0 = 1 on [0, 1),
+    evaluated at y = x + (r + 1)/2."""
+    def N(k, y):
+        if k == 0:
+            return ((y >= 0.0) & (y < 1.0)).astype(np.float64)
+        return (y * N(k - 1, y) + (k + 1 - y) * N(k - 1, y - 1.0)) / k
+    return N(r, np.asarray(x, dtype=np.float64) + 0.5 * (r + 1))
+
+
+def bspline_deriv(x, r):
+    """d/dx of the centred B-spline of degree r >= 1: N_r'(y) = N_{r-1}(y) - N_{r-1}(y - 1) on
+    y = x + (r + 1)/2, i.e. S_{r-1}(x + 1/2) - S_{r-1}(x - 1/2) (right-continuous at knots)."""
+    x = np.asarray(x, dtype=np.float64)
+    return bspline(x + 0.5, r - 1) - bspline(x - 0.5, r - 1)
+
+
 def breakpoints(xi0, beta, split=True):
     """Sorted breakpoints 0 = s_0 <= s_1 <= ... <= s_M = 1 of each orbit (§4.7, Eq. (breakpoint-set)).
 
@@ -133,36 +157,38 @@ def closed_form_weights(xi0, beta, grid, split=True, with_gradient=True):
     )
 
 
-def point_shape(xi, grid):
-    """Point values of the 8 linear B-splines around ``xi`` (§2.3, Eq. (Ah-mesh)).
+def point_shape(xi, grid, order=1):
+    """Point values of the (r + 1)^3 tensor-product B-splines of degree r = ``order`` that are
+    non-zero around ``xi`` (§2.3, Eq. (Ah-mesh)).
 
-    Returns (nodes (np,8,3), S (np,8), dS (np,8,3)) with dS[..., j] = d S_g / d x_j.
-    The cell is floor(xi); on a knot the derivative is taken from the cell above.
+    Returns (nodes (np, K, 3), S (np, K), dS (np, K, 3)) with K = (r + 1)^3 and
+    dS[..., j] = d S_g / d x_j.  The nodes are those of the knot interval holding xi; on a knot
+    the derivative is taken from the interval above.
     """
-    cell = np.floor(xi).astype(np.int64)
-    r = xi - cell
+    first = np.floor(xi - knot_offset(order)).astype(np.int64) - (order - 1) // 2
     nodes, S, dS = [], [], []
-    for nu in np.ndindex(2, 2, 2):
-        w = [(1.0 - r[:, a]) if nu[a] == 0 else r[:, a] for a in range(3)]
-        dw = [(-1.0 if nu[a] == 0 else 1.0) / grid.H[a] for a in range(3)]
-        nodes.append(_wrap(cell + np.asarray(nu, dtype=np.int64), grid.n))
+    for nu in np.ndindex(order + 1, order + 1, order + 1):
+        g = first + np.asarray(nu, dtype=np.int64)
+        w = [bspline(xi[:, a] - g[:, a], order) for a in range(3)]
+        dw = [bspline_deriv(xi[:, a] - g[:, a], order) / grid.H[a] for a in range(3)]
+        nodes.append(_wrap(g, grid.n))
         S.append(w[0] * w[1] * w[2])
         dS.append(np.stack([dw[0] * w[1] * w[2], w[0] * dw[1] * w[2], w[0] * w[1] * dw[2]], axis=1))
     return np.stack(nodes, axis=1), np.stack(S, axis=1), np.stack(dS, axis=1)
 
 
-def gauss_weights(xi0, beta, grid, nq=16, split=True):
+def gauss_weights(xi0, beta, grid, nq=16, split=True, order=1):
     """Orbit integrals by an n_q-point Gauss-Legendre rule on every segment (§4.7, §5.4).
 
-    With ``split=True`` the rule is applied on each knot-free segment, where it is exact
-    for 2 n_q - 1 >= 3r (r = 1 here); with ``split=False`` one rule covers the whole
-    path [0, 1], which is the unsplit comparison run.  The integrands are the point
-    shape S_g(x(s)) and A_{l,g}(s) d_j S_g(x(s)) themselves, evaluated at each node.
+    With ``split=True`` the rule is applied on each knot-free segment (knots of the degree-r
+    spline, r = ``order``), where it is exact for 2 n_q - 1 >= 3r; with ``split=False`` one
+    rule covers the whole path [0, 1], which is the unsplit comparison run.  The integrands
+    are the point shape S_g(x(s)) and A_{l,g}(s) d_j S_g(x(s)) themselves.
     """
     t, wq = np.polynomial.legendre.leggauss(nq)
     t = 0.5 * (t + 1.0)
     wq = 0.5 * wq
-    s = breakpoints(xi0, beta, split)
+    s = breakpoints(xi0 - knot_offset(order), beta, split)
     sm = s[:, :-1]
     h = s[:, 1:] - s[:, :-1]
     npart, M = sm.shape
@@ -171,7 +197,7 @@ def gauss_weights(xi0, beta, grid, nq=16, split=True):
         for q in range(nq):
             sq = sm[:, m] + h[:, m] * t[q]
             xq = xi0 + sq[:, None] * beta
-            nd, Sv, dS = point_shape(xq, grid)
+            nd, Sv, dS = point_shape(xq, grid, order)
             fac = (h[:, m] * wq[q])[:, None]
             nodes.append(nd)
             W.append(fac * Sv)
@@ -230,7 +256,7 @@ def orbit_gradient(An, An1, ow):
     return DA
 
 
-def point_gather(G, xi, grid):
+def point_gather(G, xi, grid, order=1):
     """Mesh interpolant G_h(x) = sum_g G_g S_g(x) at points (Eq. (Ah-mesh))."""
-    nodes, S, _ = point_shape(xi, grid)
+    nodes, S, _ = point_shape(xi, grid, order)
     return np.sum(_take(G, nodes) * S, axis=-1)

@@ -75,6 +75,7 @@ class Config:
     quadrature: str = "closed"   # "closed" (Appendices A/B) or "gauss" (§4.7 split Gauss rule)
     nq: int = 16
     n0: float = 1.0              # ion background density (§5.4)
+    order: int = 1               # B-spline degree r (1, 2, 3); r > 1 needs quadrature "gauss"
 
     def grid(self):
         return mesh.Grid(self.n, self.L)
@@ -105,9 +106,11 @@ def wrap_cells(xi, n):
 
 def orbit_weights(xi0, beta, cfg, grid, with_gradient=True):
     if cfg.quadrature == "closed":
+        if cfg.order != 1:
+            raise ValueError("the closed forms of Appendices A/B are for linear splines (order 1)")
         return orbit.closed_form_weights(xi0, beta, grid, cfg.split, with_gradient)
     if cfg.quadrature == "gauss":
-        return orbit.gauss_weights(xi0, beta, grid, cfg.nq, cfg.split)
+        return orbit.gauss_weights(xi0, beta, grid, cfg.nq, cfg.split, cfg.order)
     raise ValueError(cfg.quadrature)
 
 
@@ -118,11 +121,11 @@ def _chunks(npart):
 
 # --- Initial data (§5.4) ---------------------------------------------------------------
 
-def point_deposit(xi, q, grid):
+def point_deposit(xi, q, grid, order=1):
     """rho_e,g = sum_i q S_g(x_i) / dV (Eq. (source-moments), with the 1/dV of Eq. (orbit-current))."""
     rho = np.zeros(grid.n)
     for sl in _chunks(xi.shape[0]):
-        nodes, S, _ = orbit.point_shape(xi[sl], grid)
+        nodes, S, _ = orbit.point_shape(xi[sl], grid, order)
         rho += np.bincount(orbit.flat_index(nodes, grid.n).ravel(), weights=(q * S).ravel() / grid.dV,
                            minlength=grid.ncell).reshape(grid.n)
     return rho
@@ -134,13 +137,13 @@ def init(x, v, q, m, cfg):
     H = np.asarray(grid.H)
     xi = wrap_cells(np.asarray(x, dtype=np.float64) / H, grid.n)
     v = np.array(v, dtype=np.float64)
-    rho_e = point_deposit(xi, q, grid)
+    rho_e = point_deposit(xi, q, grid, cfg.order)
     rho = rho_e + cfg.n0
     rho = rho - np.mean(rho)
     rho = mesh.project_out_null(rho, grid)
     phi = mesh.poisson(rho, cfg.sigma1, grid)
     A = np.zeros((3,) + grid.n)
-    P = m * v + q * orbit.point_gather(A, xi, grid).T
+    P = m * v + q * orbit.point_gather(A, xi, grid, cfg.order).T
     return State(xi=xi, v=v, P=P, vprev=v.copy(), q=float(q), m=float(m), phi=phi,
                  psi=np.zeros(grid.n), A=A, U=np.zeros((3,) + grid.n), rho=rho)
 
@@ -204,7 +207,7 @@ def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, d
         P1[sl] = P[sl] + dt * (-q * gphibar + q * DAT_vbar)          # Eq. (orbit-P-update)
         xend = xi[sl] + beta[sl]                                     # Eq. (orbit-x-update), unwrapped
         xi1[sl] = wrap_cells(xend, grid.n)
-        A_end = orbit.point_gather(A1, xi1[sl], grid).T              # A_h^{n+1}(x^{n+1})
+        A_end = orbit.point_gather(A1, xi1[sl], grid, cfg.order).T   # A_h^{n+1}(x^{n+1})
         v_new[sl] = (P1[sl] - q * A_end) / m                         # Eq. (orbit-v-update)
         if slide is not None:
             sv = slide[sl]
@@ -212,7 +215,7 @@ def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, d
             P1[sl] = np.where(sv, m * v_new[sl] + q * A_end, P1[sl])
         if diagnostics:
             Ubar = orbit.gather(U_half, ow).T                        # Eq. (Ubar-def)
-            A_start = orbit.point_gather(A0, xi[sl], grid).T
+            A_start = orbit.point_gather(A0, xi[sl], grid, cfg.order).T
             DA_vbar = np.einsum("ilj,ij->il", DA, vbar[sl])          # (D A) vbar
             diag["RA"][sl] = A_end - A_start - dt * (Ubar + DA_vbar)     # Eq. (RA-test)
             diag["pu"][sl] = np.sum(ow.w, axis=1) - 1.0                  # Appendix A partition of unity
@@ -224,11 +227,12 @@ def push_particles(xi, v, P, v_it, q, m, A0, A1, gphi_half, U_half, cfg, grid, d
     return out
 
 
-def creeping(xi, beta):
+def creeping(xi, beta, order=1):
     """Particles that, on an axis with |beta_a| < BETA_CREEP (cells), get within 2 |beta_a| of
     the next knot ahead (d in (0, 1]) or start within D_KNOT of any knot: the orbits that
     cross a knot while barely moving, those that nearly do, and those hovering on a knot (an
-    iterate can flip between crossing and not crossing)."""
+    iterate can flip between crossing and not crossing).  Knots of the degree-r spline."""
+    xi = xi - orbit.knot_offset(order)
     f = np.zeros(xi.shape[0], dtype=bool)
     for a in range(3):
         x, b = xi[:, a], beta[:, a]
@@ -263,7 +267,7 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
     v_next = G.copy()
     slide = np.zeros(G.shape, dtype=bool)
     beta = cfg.dt * 0.5 * (v_it + st.v) / H
-    idx = np.nonzero(creeping(st.xi, beta))[0]
+    idx = np.nonzero(creeping(st.xi, beta, cfg.order))[0]
     if idx.size == 0:
         return v_next, slide
 
@@ -276,7 +280,8 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
     u0, r0 = v_it[idx], G[idx] - v_it[idx]
     u1 = G[idx]
     # sliding probes, one axis at a time on the base vector u1
-    d_knot = np.round(x0) - x0
+    koff = orbit.knot_offset(cfg.order)
+    d_knot = np.round(x0 - koff) - (x0 - koff)
     near = np.abs(d_knot) < D_KNOT
     u_land = 2.0 * d_knot * H / cfg.dt - vn
     sl = np.zeros(u1.shape, dtype=bool) if pinned is None else pinned[idx].copy()
