@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--shape-order", type=int, default=1, choices=[1, 2, 3],
+                    help="B-spline degree r; r > 1 runs the split Gauss rule with 2 nq - 1 >= 3 r (FP64)")
     return ap.parse_args()
 
 
@@ -275,8 +277,11 @@ def main():
 
     def timed(precision, with_clocks):
         """W warm-up steps, then K timed steps between barriers, CUDA events on the library's stream."""
+        extra = {}
+        if args.shape_order > 1:
+            extra = dict(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
         cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
-                                     precision=1 if precision == "mixed" else 0)
+                                     precision=1 if precision == "mixed" else 0, **extra)
         sm = sim.PicSim(cfg, x, v, q, m)
         e_start = sm.energy().total
         if args.warmup > 0:
@@ -316,6 +321,8 @@ def main():
     mean_pieces = prof.push_pieces / pushes if pushes else None
     push_s = prof.push_ms / 1e3
     achieved = flops / push_s / 1e12 if push_s > 0 else None
+    if args.shape_order > 1:
+        achieved = None   # the flop counts above are those of the linear closed forms
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": KPUSH_TRAFFIC_BYTES.get(w.name) if args.precision == "fp64" else None,
@@ -358,7 +365,7 @@ def main():
 
     # the other precision on the same workload ("mixed vs FP64 at stated energy drift")
     other = None
-    if args.precision == "fp64" and not args.no_mixed:
+    if args.precision == "fp64" and not args.no_mixed and args.shape_order == 1:
         sm2, inf2, pr2, ms2, drift2, _ = timed("mixed", False)
         sm2.close()
         # per particle-iteration: read cell 4 + offset 12 + v^n 12 + increment 12, write 12
@@ -396,7 +403,10 @@ def main():
                        "picard_tol": w.picard_tol,
                        "precision": "fp64" if args.precision == "fp64" else
                                     "mixed: FP32 iterations, FP64 refinement and final sweep",
-                       "orbits": "split at knots, closed form",
+                       "orbits": ("split at knots, closed form" if args.shape_order == 1 else
+                                  f"split at the knots of the degree-{args.shape_order} B-spline, "
+                                  f"{(3 * args.shape_order + 2) // 2}-point Gauss rule per piece"),
+                       "shape_order": args.shape_order,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": f"inputs larger than L2 (FP64 particle state {w.n_particles * 120 / 1e9:.1f} GB "
                              f"per GPU: x, v, P, v^(n-1), iterate)",

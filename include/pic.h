@@ -94,6 +94,12 @@ typedef struct {
                                      grids are the defaults (pic_autotune changes nothing).  The
                                      same inputs then give the same bits, run after run and alone
                                      or in an ensemble.  Needs |v| < 100 kappa. */
+    int32_t shape_order;          /* B-spline degree r of the particle shape: 1 (default, the
+                                     paper's test), 2 or 3 (§4.7, Table 2).  Nodes at the
+                                     integers; knots at the integers for odd r and at the
+                                     half-integers for even r; orbits are split at those knots.
+                                     r > 1 needs quadrature = PIC_QUAD_GAUSS (exact on every
+                                     piece when 2 nq - 1 >= 3 r) and precision = PIC_FP64 */
 } pic_config;
 
 /* Initial particles of one species. */
@@ -184,7 +190,7 @@ typedef struct {
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
  * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
- * at most 8 FP32 iterations, not deterministic. */
+ * at most 8 FP32 iterations, not deterministic, linear shapes (r = 1). */
 pic_status pic_config_default(pic_config* cfg);
 
 /* Create a context: copies the particles to the device, sorts them by cell, deposits

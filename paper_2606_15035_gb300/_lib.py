@@ -58,6 +58,7 @@ class PicConfig(C.Structure):
         ("mixed_tol32", C.c_double),
         ("mixed_max32", C.c_int32),
         ("deterministic", C.c_int32),
+        ("shape_order", C.c_int32),
     ]
 
 

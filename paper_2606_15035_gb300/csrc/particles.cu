@@ -100,11 +100,110 @@ __device__ __forceinline__ int scatter_gauss(const StepParams& p, const double x
     });
 }
 
+// ---- shapes of degree R = 2, 3 (§4.7) ---------------------------------------------------
+//
+// One axis of the tensor-product B-spline of degree R at x (cell units): the R + 1 non-zero
+// values, their x-derivatives and the first node.  The nodes sit at the integers, the knots
+// at the integers (odd R) or the half-integers (even R); on the knot interval holding x, in
+// its local coordinate t in [0, 1), the centred cardinal B-spline's pieces are
+//   R = 2:  (1 - t)^2 / 2,  1/2 + t (1 - t),  t^2 / 2;
+//   R = 3:  (1 - t)^3 / 6,  (3 t^3 - 6 t^2 + 4) / 6,  (-3 t^3 + 3 t^2 + 3 t + 1) / 6,  t^3 / 6.
+template <int R>
+struct Basis1 {
+    double w[R + 1], dw[R + 1];
+    int first;
+};
+
+template <int R>
+__device__ __forceinline__ void basis1(double x, double invH, Basis1<R>& b) {
+    const double xs = (R % 2 == 0) ? x - 0.5 : x;
+    const double f = floor(xs), t = xs - f, u = 1.0 - t;
+    b.first = (int)f - (R - 1) / 2;
+    if constexpr (R == 2) {
+        b.w[0] = 0.5 * u * u;
+        b.w[1] = 0.5 + t * u;
+        b.w[2] = 0.5 * t * t;
+        b.dw[0] = -u * invH;
+        b.dw[1] = (u - t) * invH;
+        b.dw[2] = t * invH;
+    } else {
+        const double t2 = t * t, t3 = t2 * t;
+        b.w[0] = u * u * u * (1.0 / 6.0);
+        b.w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) * (1.0 / 6.0);
+        b.w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) * (1.0 / 6.0);
+        b.w[3] = t3 * (1.0 / 6.0);
+        b.dw[0] = -0.5 * u * u * invH;
+        b.dw[1] = (1.5 * t2 - 2.0 * t) * invH;
+        b.dw[2] = (-1.5 * t2 + t + 0.5) * invH;
+        b.dw[3] = 0.5 * t2 * invH;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void basis3(const StepParams& p, const double x[3], Basis1<R> b[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) basis1<R>(x[a], p.invH[a], b[a]);
+}
+
+// Visit the (R + 1)^3 nodes of the shape at a point: f(node row, S_g, grad S_g).
+template <int R, typename F>
+__device__ __forceinline__ void for_each_node(const StepParams& p, const Basis1<R> b[3], F&& f) {
+    for (int iz = 0; iz <= R; ++iz) {
+        const int gz = wrapi(b[2].first + iz, p.m.n[2]);
+        for (int iy = 0; iy <= R; ++iy) {
+            const int gy = wrapi(b[1].first + iy, p.m.n[1]);
+            const double wyz = b[1].w[iy] * b[2].w[iz];
+            const double dy = b[1].dw[iy] * b[2].w[iz], dz = b[1].w[iy] * b[2].dw[iz];
+#pragma unroll
+            for (int ix = 0; ix <= R; ++ix) {
+                const int gx = wrapi(b[0].first + ix, p.m.n[0]);
+                const double wx = b[0].w[ix];
+                const double dS[3] = {b[0].dw[ix] * wyz, wx * dy, wx * dz};
+                f(node_index(gx, gy, gz, p.m), wx * wyz, dS);
+            }
+        }
+    }
+}
+
+// The orbit current with an n_q-point Gauss rule on each piece between the knots of the
+// degree-R shape (split) or on the whole path (unsplit).
+template <int R>
+__device__ __forceinline__ int scatter_gauss_r(const StepParams& p, const double x0[3], const double beta[3],
+                                               const double w[3], double* __restrict__ J) {
+    const int64_t N = p.m.ncell;
+    const double xs[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};
+    return for_each_segment(xs, beta, p.split != 0, [&](const Segment<double>& sg) {
+        for (int qd = 0; qd < p.nq; ++qd) {
+            const double s = sg.s0 + sg.h * c_gauss_t[qd];
+            const double wq = sg.h * c_gauss_w[qd];
+            const double xq[3] = {x0[0] + s * beta[0], x0[1] + s * beta[1], x0[2] + s * beta[2]};
+            Basis1<R> b[3];
+            basis3<R>(p, xq, b);
+            for_each_node<R>(p, b, [&](int64_t g, double S, const double*) {
+                const double f = wq * S;
+                if (p.det) {
+                    exact_add(p.acc, g, w[0] * f);
+                    exact_add(p.acc, N + g, w[1] * f);
+                    exact_add(p.acc, 2 * N + g, w[2] * f);
+                } else {
+                    atomicAdd(J + g, w[0] * f);
+                    atomicAdd(J + N + g, w[1] * f);
+                    atomicAdd(J + 2 * N + g, w[2] * f);
+                }
+            });
+        }
+    });
+}
+
 template <int QUAD>
 __device__ __forceinline__ int scatter_orbit(const StepParams& p, const double x0[3], const double beta[3],
                                              const double w[3], double* J) {
     if constexpr (QUAD == 0) return scatter_closed(p, x0, beta, w, J);
-    else return scatter_gauss(p, x0, beta, w, J);
+    else {
+        if (p.order == 2) return scatter_gauss_r<2>(p, x0, beta, w, J);
+        if (p.order == 3) return scatter_gauss_r<3>(p, x0, beta, w, J);
+        return scatter_gauss(p, x0, beta, w, J);
+    }
 }
 
 // ---- push (Eq. (orbit-push)) -------------------------------------------------------
@@ -285,20 +384,70 @@ __device__ __forceinline__ void push_piece_gauss(const StepParams& p, const Segm
     }
 }
 
+// The Gauss-rule piece of push_piece_gauss for the degree-R shape.
+template <int R, bool DIAG>
+__device__ __forceinline__ void push_piece_gauss_r(const StepParams& p, const Segment<double>& sg, const double x0[3],
+                                                   const double beta[3], const double vb[3],
+                                                   const double* __restrict__ table, PushAcc& acc) {
+    for (int qd = 0; qd < p.nq; ++qd) {
+        const double s = sg.s0 + sg.h * c_gauss_t[qd];
+        const double wq = sg.h * c_gauss_w[qd];
+        const double xq[3] = {x0[0] + s * beta[0], x0[1] + s * beta[1], x0[2] + s * beta[2]};
+        Basis1<R> b[3];
+        basis3<R>(p, xq, b);
+        for_each_node<R>(p, b, [&](int64_t g, double S, const double* dS) {
+            const double W = wq * S;
+            const double dW[3] = {wq * dS[0], wq * dS[1], wq * dS[2]};
+            const double* t = table + 12 * g;
+            const double an = t[0] * vb[0] + t[1] * vb[1] + t[2] * vb[2];
+            const double a1 = t[3] * vb[0] + t[4] * vb[1] + t[5] * vb[2];
+            const double as = (1.0 - s) * an + s * a1;           // A_g(s) . vbar
+            acc.gphi[0] += W * t[6];
+            acc.gphi[1] += W * t[7];
+            acc.gphi[2] += W * t[8];
+            acc.F[0] += as * dW[0];
+            acc.F[1] += as * dW[1];
+            acc.F[2] += as * dW[2];
+            if constexpr (DIAG) {
+                acc.Ubar[0] += W * t[9];
+                acc.Ubar[1] += W * t[10];
+                acc.Ubar[2] += W * t[11];
+                acc.pu += W;
+                const double vdW = vb[0] * dW[0] + vb[1] * dW[1] + vb[2] * dW[2];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) acc.DAv[l] += ((1.0 - s) * t[l] + s * t[3 + l]) * vdW;
+            }
+        });
+    }
+}
+
 // Point interpolant of columns [col, col+3) of the table at a wrapped position.
 __device__ __forceinline__ void point_gather3(const StepParams& p, const double xq[3], const double* __restrict__ table,
                                               int col, double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    auto add = [&](int64_t g, double S, const double*) {
+        const double* t = table + 12 * g + col;
+        out[0] += S * t[0];
+        out[1] += S * t[1];
+        out[2] += S * t[2];
+    };
+    if (p.order == 2) {
+        Basis1<2> b[3];
+        basis3<2>(p, xq, b);
+        for_each_node<2>(p, b, add);
+        return;
+    }
+    if (p.order == 3) {
+        Basis1<3> b[3];
+        basis3<3>(p, xq, b);
+        for_each_node<3>(p, b, add);
+        return;
+    }
     int64_t g[8];
     double w[8];
     point_weights8(xq, p.m, g, w);
-    out[0] = out[1] = out[2] = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const double* t = table + 12 * g[k] + col;
-        out[0] += w[k] * t[0];
-        out[1] += w[k] * t[1];
-        out[2] += w[k] * t[2];
-    }
+    for (int k = 0; k < 8; ++k) add(g[k], w[k], nullptr);
 }
 
 template <typename T>
@@ -323,13 +472,24 @@ __global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, dou
     const int64_t np = p.np;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         double x[3] = {xi[i], xi[np + i], xi[2 * np + i]};
-        int64_t g[8];
-        double w[8];
-        point_weights8(x, p.m, g, w);
+        auto dep = [&](int64_t g, double S, const double*) {
+            if (p.det) exact_add(p.acc, g, p.q_dV * S);
+            else atomicAdd(rho + g, p.q_dV * S);
+        };
+        if (p.order == 2) {
+            Basis1<2> b[3];
+            basis3<2>(p, x, b);
+            for_each_node<2>(p, b, dep);
+        } else if (p.order == 3) {
+            Basis1<3> b[3];
+            basis3<3>(p, x, b);
+            for_each_node<3>(p, b, dep);
+        } else {
+            int64_t g[8];
+            double w[8];
+            point_weights8(x, p.m, g, w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (p.det) exact_add(p.acc, g[k], p.q_dV * w[k]);
-            else atomicAdd(rho + g[k], p.q_dV * w[k]);
+            for (int k = 0; k < 8; ++k) dep(g[k], w[k], nullptr);
         }
     }
 }
@@ -394,8 +554,12 @@ __device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3
             else push_piece_fast(p, sg, beta, vb, table, acc);
         });
     } else {
-        o.nseg = for_each_segment(x0, beta, p.split != 0, [&](const Segment<double>& sg) {
-            push_piece_gauss<DIAG>(p, sg, x0, beta, vb, table, acc);
+        // pieces between the knots of the shape's degree (shifted by 1/2 for even degrees)
+        const double xs[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};
+        o.nseg = for_each_segment(xs, beta, p.split != 0, [&](const Segment<double>& sg) {
+            if (p.order == 2) push_piece_gauss_r<2, DIAG>(p, sg, x0, beta, vb, table, acc);
+            else if (p.order == 3) push_piece_gauss_r<3, DIAG>(p, sg, x0, beta, vb, table, acc);
+            else push_piece_gauss<DIAG>(p, sg, x0, beta, vb, table, acc);
         });
     }
 #pragma unroll
@@ -456,7 +620,8 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
                 bet2[a] = p.dt * vb2 * p.invH[a];
                 wv[a] = p.q_dV * vb2;
             }
-            const bool creep = p.accel && is_creeping(x0, beta_it);
+            const double xk[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};   // knot lattice
+            const bool creep = p.accel && is_creeping(xk, beta_it);
             if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
             if (creep) {
                 if (!creep_flag) {
@@ -574,7 +739,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
         double uland[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double dk = rint(x0[a]) - x0[a];
+            const double dk = rint(x0[a] - p.koff) - (x0[a] - p.koff);   // signed distance to the nearest knot
             uland[a] = 2.0 * dk * p.H[a] / p.dt - vn[a];
             if ((slide[i] >> a) & 1u) {
                 sl[a] = true;                            // pinned earlier in this step: stays pinned
@@ -913,6 +1078,8 @@ StepParams make_params(const Ctx& c) {
     p.split = c.cfg.split_orbit_at_knots;
     p.nq = c.cfg.nq;
     p.accel = c.cfg.picard_accel;
+    p.order = c.cfg.shape_order;
+    p.koff = (c.cfg.shape_order % 2 == 0) ? 0.5 : 0.0;
     p.det = c.cfg.deterministic;
     p.acc = ExactAcc{c.acc_hi, c.acc_lo, c.inv_u_J, c.dev_status};
     return p;

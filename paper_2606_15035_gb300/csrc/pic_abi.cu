@@ -205,6 +205,8 @@ pic_status validate(const pic_config* cfg) {
         if (!(cfg->mixed_tol32 > 0.0) || cfg->mixed_max32 < 1) return PIC_ERR_ARG;
     }
     if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
+    if (cfg->shape_order < 1 || cfg->shape_order > 3) return PIC_ERR_ARG;
+    if (cfg->shape_order > 1 && (cfg->quadrature != PIC_QUAD_GAUSS || cfg->precision != PIC_FP64)) return PIC_ERR_ARG;
     return PIC_OK;
 }
 
@@ -655,6 +657,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
     cfg->deterministic = 0;
+    cfg->shape_order = 1;
     cfg->helmholtz_tol = 1e-17;
     return PIC_OK;
 }

@@ -56,6 +56,8 @@ struct StepParams {
     int split;                 // split orbits at knots
     int nq;                    // Gauss points (Gauss quadrature only)
     int accel;                 // particle-local solves for creeping particles
+    int order;                 // B-spline degree r of the shape (1, 2, 3)
+    double koff;               // knot offset: 0 (odd r, knots at the integers) or 0.5 (even r)
     int det;                   // deterministic mode: deposits go to acc (exact, order independent)
     ExactAcc acc;
 };

@@ -381,3 +381,39 @@ def test_residual_history_records_each_iteration(sim, precision):
     d = ev[f32 == 0]
     assert d[-1] < d[0] or len(d) == 1
     s.close()
+
+
+@pytest.mark.parametrize("order,split", [(2, True), (3, True), (2, False)])
+def test_higher_order_shapes_match_oracle(sim, order, split):
+    """B-spline degree r = 2, 3 (§4.7): split Gauss orbit integrals with 2 n_q - 1 >= 3 r, the
+    degree-r deposit and interpolant, orbits split at the degree-r knots (half-integers for
+    r = 2).  Matches the oracle step by step; the split runs conserve energy and keep the
+    chain rule at roundoff, the unsplit run matches the oracle's unsplit rule."""
+    n, L = (6, 5, 5), (1.2, 1.0, 1.0)
+    x, v, q, m = pi.random_twostream(n, L, 2, 0.3, 1e-2, 2e-2, 5000 + order)
+    nq = (3 * order + 2) // 2
+    cfg = sim.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-13, quadrature=1, nq=nq, shape_order=order,
+                                 split_orbit_at_knots=int(split), diagnostics=1)
+    ocfg = opic.Config(n=n, L=L, dt=0.1, picard_tol=1e-13, quadrature="gauss", nq=nq, order=order, split=split)
+    s = sim.PicSim(cfg, x, v, q, m)
+    o = opic.init(x, v, q, m, ocfg)
+    st = s.get_state()
+    assert rel(st.rho, o.rho) <= 1e-13 and rel(st.phi, o.phi) <= 1e-12
+    for _ in range(2):
+        info = s.step(1)
+        o, oinfo = opic.step(o, ocfg)
+        assert info.converged and oinfo["converged"]
+        compare_state(s.get_state(), o, ocfg, 1e-12, L)
+        d = s.diagnostics()
+        if split:
+            assert abs(d.R_total) <= 1e-13 * (d.K1 + d.W1) and d.RA_max <= 1e-13
+        assert abs(d.R_total - oinfo["R_total"]) <= 1e-12 * (d.K1 + d.W1)
+    s.close()
+
+
+def test_higher_order_shapes_need_gauss_fp64(sim):
+    x, v, q, m, n, L = c1_inputs()
+    for kw in (dict(shape_order=2), dict(shape_order=3, quadrature=1, precision=1), dict(shape_order=4, quadrature=1)):
+        cfg = sim.pic_config_default(n=n, L=L, dt=0.1, **kw)
+        with pytest.raises(sim.PicError):
+            sim.PicSim(cfg, x, v, q, m)
