@@ -8,9 +8,13 @@ Node ``g = (ix, iy, iz)`` sits at ``x_g = (ix*Hx, iy*Hy, iz*Hz)`` (node-collocat
 Spatial operators (the reading used throughout, stated in the design notes):
 the paper's theorems (§3.3 Theorem "gauge and Gauss preservation", §4.6 field energy
 balance) need periodic first-derivative operators ``D_a`` that are skew-adjoint and
-commute, and a Laplacian equal to ``sum_a D_a D_a``.  The oracle uses the
-second-order central difference ``D_a f = (f[i+1] - f[i-1]) / (2 H_a)`` and the
-matching wide Laplacian ``Delta_h = sum_a D_a D_a`` (radius-2 stencil per axis).
+commute, and a Laplacian equal to ``sum_a D_a D_a``.  Two choices are provided:
+``ops="central2"`` (default), the second-order central difference
+``D_a f = (f[i+1] - f[i-1]) / (2 H_a)`` with the matching wide Laplacian
+``Delta_h = sum_a D_a D_a`` (radius-2 stencil per axis); and ``ops="spectral"``, the
+paper's Fourier operators (§3.3): symbol ``i k_a`` with ``k_a = 2 pi m_a / L_a``, the
+Nyquist symbol (2 |m_a| = n_a) set to zero so that ``D_a`` stays real and skew-adjoint,
+and ``Delta_h = sum_a D_a D_a`` with symbol ``-sum_a k_a^2`` (zero on the same 8 modes).
 """
 
 from __future__ import annotations
@@ -21,7 +25,10 @@ import numpy as np
 class Grid:
     """Periodic box ``[0,Lx) x [0,Ly) x [0,Lz)`` with ``n = (nx, ny, nz)`` nodes (§5.4)."""
 
-    def __init__(self, n, L):
+    def __init__(self, n, L, ops="central2"):
+        if ops not in ("central2", "spectral"):
+            raise ValueError(ops)
+        self.ops = ops
         self.n = tuple(int(v) for v in n)
         self.L = tuple(float(v) for v in L)
         self.H = tuple(self.L[a] / self.n[a] for a in range(3))
@@ -41,16 +48,19 @@ class Grid:
         return th
 
     def d_symbol(self, a):
-        """Symbol of the central difference D_a acting on exp(i theta x/H): i sin(theta)/H."""
+        """Symbol of D_a acting on exp(i theta x/H): i sin(theta)/H (central difference), or
+        i k = i theta / H with the Nyquist mode set to 0 (spectral)."""
         th = self.wavenumbers()[a]
-        return 1j * np.sin(th) / self.H[a]
+        if self.ops == "central2":
+            return 1j * np.sin(th) / self.H[a]
+        m = np.rint(th * self.n[a] / (2.0 * np.pi))
+        return np.where(2 * np.abs(m) == self.n[a], 0.0, 1j * th / self.H[a])
 
     def lap_symbol(self):
-        """Symbol of Delta_h = sum_a D_a D_a: -sum_a sin^2(theta_a)/H_a^2 (<= 0)."""
-        th = self.wavenumbers()
+        """Symbol of Delta_h = sum_a D_a D_a (<= 0): the sum of the squared D_a symbols."""
         s = np.zeros(self.n)
         for a in range(3):
-            s = s - (np.sin(th[a]) / self.H[a]) ** 2
+            s = s + np.real(self.d_symbol(a) ** 2)
         return s
 
     def null_mask(self):
@@ -69,8 +79,11 @@ class Grid:
 # --- Real-space stencil operators (§3.2, §4.1) ----------------------------------------
 
 def d(f, a, grid):
-    """Central difference along axis ``a``: (f[i+1] - f[i-1]) / (2 H_a), periodic."""
-    return (np.roll(f, -1, axis=a) - np.roll(f, 1, axis=a)) / (2.0 * grid.H[a])
+    """D_a along axis ``a``: the central difference (f[i+1] - f[i-1]) / (2 H_a), periodic, or
+    (spectral) multiplication of the Fourier coefficients by the D_a symbol."""
+    if grid.ops == "central2":
+        return (np.roll(f, -1, axis=a) - np.roll(f, 1, axis=a)) / (2.0 * grid.H[a])
+    return np.real(np.fft.ifftn(grid.d_symbol(a) * np.fft.fftn(f)))
 
 
 def grad(f, grid):

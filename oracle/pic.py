@@ -76,9 +76,10 @@ class Config:
     nq: int = 16
     n0: float = 1.0              # ion background density (§5.4)
     order: int = 1               # B-spline degree r (1, 2, 3); r > 1 needs quadrature "gauss"
+    ops: str = "central2"        # spatial operators: "central2" or "spectral" (§3.3)
 
     def grid(self):
-        return mesh.Grid(self.n, self.L)
+        return mesh.Grid(self.n, self.L, self.ops)
 
 
 @dataclass
