@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--ops", default="central2", choices=["central2", "spectral"],
+                    help="spatial operators: central differences or the paper's spectral operators (FFT)")
     ap.add_argument("--shape-order", type=int, default=1, choices=[1, 2, 3],
                     help="B-spline degree r; r > 1 runs the split Gauss rule with 2 nq - 1 >= 3 r (FP64)")
     return ap.parse_args()
@@ -277,9 +279,9 @@ def main():
 
     def timed(precision, with_clocks):
         """W warm-up steps, then K timed steps between barriers, CUDA events on the library's stream."""
-        extra = {}
+        extra = {"ops": 1 if args.ops == "spectral" else 0}
         if args.shape_order > 1:
-            extra = dict(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
+            extra.update(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
         cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
                                      precision=1 if precision == "mixed" else 0, **extra)
         sm = sim.PicSim(cfg, x, v, q, m)
@@ -407,6 +409,7 @@ def main():
                                   f"split at the knots of the degree-{args.shape_order} B-spline, "
                                   f"{(3 * args.shape_order + 2) // 2}-point Gauss rule per piece"),
                        "shape_order": args.shape_order,
+                       "ops": args.ops,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": f"inputs larger than L2 (FP64 particle state {w.n_particles * 120 / 1e9:.1f} GB "
                              f"per GPU: x, v, P, v^(n-1), iterate)",

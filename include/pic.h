@@ -100,7 +100,16 @@ typedef struct {
                                      half-integers for even r; orbits are split at those knots.
                                      r > 1 needs quadrature = PIC_QUAD_GAUSS (exact on every
                                      piece when 2 nq - 1 >= 3 r) and precision = PIC_FP64 */
+    int32_t ops;                  /* spatial operators: PIC_OPS_CENTRAL2 (default; D_a the central
+                                     difference, Delta_h = sum_a D_a D_a) or PIC_OPS_SPECTRAL (the
+                                     paper's Fourier operators, §3.3: D_a = i k_a with the Nyquist
+                                     symbol zero, Delta_h = -|k|^2; the CN update is then solved
+                                     exactly per mode by FFT).  Spectral needs every n_a = 2^p 3^q
+                                     <= 1024 */
 } pic_config;
+
+#define PIC_OPS_CENTRAL2 0
+#define PIC_OPS_SPECTRAL 1
 
 /* Initial particles of one species. */
 typedef struct {
@@ -190,7 +199,7 @@ typedef struct {
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
  * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
- * at most 8 FP32 iterations, not deterministic, linear shapes (r = 1). */
+ * at most 8 FP32 iterations, not deterministic, linear shapes (r = 1), central-difference operators. */
 pic_status pic_config_default(pic_config* cfg);
 
 /* Create a context: copies the particles to the device, sorts them by cell, deposits

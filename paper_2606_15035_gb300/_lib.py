@@ -28,6 +28,7 @@ STATUS_NAMES = {
 }
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
+PIC_OPS_CENTRAL2, PIC_OPS_SPECTRAL = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
             "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile", "pic_residual_history",
@@ -59,6 +60,7 @@ class PicConfig(C.Structure):
         ("mixed_max32", C.c_int32),
         ("deterministic", C.c_int32),
         ("shape_order", C.c_int32),
+        ("ops", C.c_int32),
     ]
 
 

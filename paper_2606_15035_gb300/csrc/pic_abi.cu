@@ -206,6 +206,12 @@ pic_status validate(const pic_config* cfg) {
     }
     if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
     if (cfg->shape_order < 1 || cfg->shape_order > 3) return PIC_ERR_ARG;
+    if (cfg->ops != PIC_OPS_CENTRAL2 && cfg->ops != PIC_OPS_SPECTRAL) return PIC_ERR_ARG;
+    if (cfg->ops == PIC_OPS_SPECTRAL) {
+        int radix[FFT_MAX_STAGES], nst = 0;
+        for (int a = 0; a < 3; ++a)
+            if (!fft_factor(cfg->n[a], radix, nst)) return PIC_ERR_ARG;
+    }
     if (cfg->shape_order > 1 && (cfg->quadrature != PIC_QUAD_GAUSS || cfg->precision != PIC_FP64)) return PIC_ERR_ARG;
     return PIC_OK;
 }
@@ -314,6 +320,21 @@ pic_status allocate(pic_ctx* ctx) {
         c.inv_u_J = inv_u(wq * 100.0 * c.cfg.kappa);
         c.inv_u_rho = inv_u(wq);
     }
+    if (c.cfg.ops == PIC_OPS_SPECTRAL) {
+        ALLOC(c.spec0, double2, 9 * N);
+        ALLOC(c.spec1, double2, 12 * N);
+        ALLOC(c.specJ, double2, 3 * N);
+        ALLOC(c.specR, double2, 3 * N);
+        ALLOC(c.spec_gphi, double, 3 * N);
+        for (int a = 0; a < 3; ++a) {
+            fft_factor(c.m.n[a], c.fft_radix[a], c.fft_nst[a]);
+            std::vector<double2> tw;
+            spec_twiddles(c.m.n[a], tw);
+            ALLOC(c.fft_tw[a], double2, c.m.n[a]);
+            cudaMemcpyAsync(c.fft_tw[a], tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, c.stream);
+            if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "twiddles");
+        }
+    }
     ALLOC(c.partials, double, (size_t)NSLOT * MAX_BLOCKS);
     ALLOC(c.results, double, NSLOT);
     ALLOC(c.dev_status, int, 1);
@@ -332,6 +353,10 @@ pic_status allocate(pic_ctx* ctx) {
 pic_status solve_poisson(pic_ctx* ctx) {
     Ctx& c = ctx->c;
     const int64_t N = c.m.ncell;
+    if (c.cfg.ops == PIC_OPS_SPECTRAL) {
+        launch_spec_poisson(c);
+        return check_cuda(ctx, "poisson");
+    }
     double lmax = 0.0, lmin = 0.0;
     for (int ax = 0; ax < 3; ++ax) {
         double mx, mn;
@@ -366,8 +391,16 @@ namespace {
 void queue_energy(Ctx& c) {
     launch_kinetic(c);
     launch_finalize(c, S_K, 1, particle_blocks(c), false);
-    launch_mesh_energy(c, c.F0, c.W0, S_W0);
+    if (c.cfg.ops == PIC_OPS_SPECTRAL) launch_spec_energy(c, c.F0, c.W0, S_W0);
+    else launch_mesh_energy(c, c.F0, c.W0, S_W0);
     launch_finalize(c, S_W0, 1, mesh_blocks(c), false);
+}
+
+// Per-step mesh set-up: the CN right-hand-side part of level n (stencils), or the transforms
+// of level n (spectral operators).
+void mesh_begin(Ctx& c) {
+    if (c.cfg.ops == PIC_OPS_SPECTRAL) launch_spec_begin(c);
+    else launch_rhs0(c);
 }
 
 // The mesh half of one Algorithm 1 iteration: continuity, CN solve (warm-started from F1),
@@ -375,6 +408,10 @@ void queue_energy(Ctx& c) {
 void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev) {
     const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
     ProfScope ps(c, PH_MESH);
+    if (c.cfg.ops == PIC_OPS_SPECTRAL) {
+        launch_spec_mesh_phase(c, Jcur, Jprev);
+        return;
+    }
     launch_source(c, Jcur, Jprev);
     launch_helmholtz(c, c.rhs, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, &c.F1, &c.F1b);
     launch_backsub_table(c, false);
@@ -397,7 +434,7 @@ void step_begin(Ctx& c) {
         launch_sort(c);
     }
     if (c.cfg.diagnostics) queue_energy(c);
-    launch_rhs0(c);
+    mesh_begin(c);
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
     if (np > 0) cudaMemsetAsync(c.slide, 0, (size_t)np, c.stream);   // sliding marks live one step
     c.hist_ev.clear();
@@ -557,7 +594,8 @@ void final_issue(Ctx& c) {
     if (diag) {
         launch_finalize(c, S_K1, 3, particle_blocks(c), false);   // K1, PWORK, RA_SQ
         launch_finalize(c, S_RA_MAX, 2, particle_blocks(c), true);
-        launch_mesh_diag(c, Jfin);
+        if (c.cfg.ops == PIC_OPS_SPECTRAL) launch_spec_diag(c, Jfin);
+        else launch_mesh_diag(c, Jfin);
         launch_finalize(c, S_MWORK, 2, mesh_blocks(c), false);    // MWORK, W
         launch_finalize(c, S_G_MAX, 1, mesh_blocks(c), true);
         launch_finalize(c, S_G_SQ, 1, mesh_blocks(c), false);
@@ -658,6 +696,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->mixed_max32 = 8;
     cfg->deterministic = 0;
     cfg->shape_order = 1;
+    cfg->ops = PIC_OPS_CENTRAL2;
     cfg->helmholtz_tol = 1e-17;
     return PIC_OK;
 }
@@ -837,7 +876,7 @@ pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, co
         launch_permute_in(c, c.vnew, c.sort_tmp, 1.0, 1.0, 1.0);   // caller order -> device order
         vgiven = c.sort_tmp;
     }
-    launch_rhs0(c);
+    mesh_begin(c);
     cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
     cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
     if (np > 0) launch_first_scatter(c, c.J[0], vgiven);
@@ -985,7 +1024,7 @@ pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push
         // everything written is scratch (iterates, next current, creeping list), nothing of
         // the committed state changes.
         const int64_t N = c.m.ncell;
-        launch_rhs0(c);
+        mesh_begin(c);
         cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
         cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
         launch_first_scatter(c, c.J[0], nullptr);

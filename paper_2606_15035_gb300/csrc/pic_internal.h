@@ -62,6 +62,9 @@ struct StepParams {
     ExactAcc acc;
 };
 
+constexpr int FFT_MAX = 1024;       // largest mesh size per axis with spectral operators
+constexpr int FFT_MAX_STAGES = 16;
+
 // Host-side state of the time step in progress (see step_begin / iter_issue / iter_finish).
 struct StepRun {
     int cur = 0, prev = 1, next = 2;   // J buffers: current iterate, previous, next
@@ -118,6 +121,14 @@ struct Ctx {
     std::vector<double> hist_ev, hist_eJ;   // residuals of the last step's iterations
     std::vector<int32_t> hist_fp32;
     StepRun run;
+    // spectral operators (ops = PIC_OPS_SPECTRAL): transforms of level n [phi, A | psi, U | rho]
+    // (9 N), of level n+1 and D phi^{n+1/2} (12 N), of J (3 N), residual scratch (3 N), the
+    // real D phi^{n+1/2} (3 N), and the FFT plan of each axis
+    double2 *spec0 = nullptr, *spec1 = nullptr, *specJ = nullptr, *specR = nullptr;
+    double* spec_gphi = nullptr;
+    double2* fft_tw[3] = {nullptr, nullptr, nullptr};
+    int fft_radix[3][FFT_MAX_STAGES] = {};
+    int fft_nst[3] = {0, 0, 0};
     // deterministic mode: exact deposit accumulators (3 N each), their scales, creeping flags,
     // and the radix-sort work arrays
     long long *acc_hi = nullptr, *acc_lo = nullptr;
@@ -174,6 +185,14 @@ void launch_to32(Ctx& c);
 void launch_scatter32(Ctx& c, double* J);
 void launch_push32(Ctx& c, double* Jnext);
 void launch_exact_finish(Ctx& c, double* out, int64_t n, double inv_u);   // acc -> out, acc = 0
+// spectral operators (spectral.cu)
+bool fft_factor(int n, int* radix, int& nst);
+void spec_twiddles(int n, std::vector<double2>& tw);
+void launch_spec_begin(Ctx& c);
+void launch_spec_mesh_phase(Ctx& c, const double* Jcur, const double* Jprev);
+void launch_spec_energy(Ctx& c, const double* F, const double* W, int slot);
+void launch_spec_diag(Ctx& c, const double* Jfinal);
+void launch_spec_poisson(Ctx& c);
 int radix_tiles(int64_t np);
 int push32_blocks(const Ctx& c);   // grid of the FP32 chunk kernels (partials per block)
 void launch_table32(Ctx& c);

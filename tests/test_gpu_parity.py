@@ -417,3 +417,39 @@ def test_higher_order_shapes_need_gauss_fp64(sim):
         cfg = sim.pic_config_default(n=n, L=L, dt=0.1, **kw)
         with pytest.raises(sim.PicError):
             sim.PicSim(cfg, x, v, q, m)
+
+
+@pytest.mark.parametrize("n,precision", [((8, 8, 8), 0), ((6, 9, 4), 0), ((8, 8, 8), 1)])
+def test_spectral_operators_match_oracle(sim, n, precision):
+    """ops = PIC_OPS_SPECTRAL (§3.3): FFT-based continuity and exact per-mode CN update (radix-2
+    and radix-3 meshes).  Init, every step's state and the diagnostics match the oracle's
+    spectral operators; energy, gauge and Gauss residuals stay at roundoff."""
+    side = (1.2, 1.0, 0.9)
+    x, v, q, m = pi.random_twostream(n, side, 4, 0.25, 1e-2, 1e-2, 6000 + n[1])
+    cfg = sim.pic_config_default(n=n, L=side, dt=0.1, picard_tol=1e-13, ops=1, precision=precision, diagnostics=1)
+    ocfg = opic.Config(n=n, L=side, dt=0.1, picard_tol=1e-13, ops="spectral")
+    s = sim.PicSim(cfg, x, v, q, m)
+    o = opic.init(x, v, q, m, ocfg)
+    st = s.get_state()
+    assert rel(st.rho, o.rho) <= 1e-13 and rel(st.phi, o.phi) <= 1e-12
+    e = s.energy()
+    K0, W0 = opic.energy(o, ocfg)
+    assert abs(e.W - W0) <= 1e-12 * (K0 + W0)
+    tol = 1e-12 if precision == 0 else 1e-11
+    for _ in range(3):
+        info = s.step(1)
+        o, oinfo = opic.step(o, ocfg)
+        assert info.converged and oinfo["converged"]
+        compare_state(s.get_state(), o, ocfg, tol, side)
+        d = s.diagnostics()
+        assert abs(d.R_total) <= 1e-13 * (d.K1 + d.W1) and d.RA_max <= 1e-14
+        assert abs(d.W1 - oinfo["W1"]) <= 1e-12 * (d.K1 + d.W1)
+        assert d.gauge_max <= 1e-10 and d.gauss_max <= 1e-9 and d.continuity_max <= 1e-10
+    s.close()
+
+
+def test_spectral_operators_reject_other_mesh_sizes(sim):
+    x, v, q, m = pi.random_twostream((5, 8, 8), (1.0, 1.0, 1.0), 2, 0.2, 1e-3, 0.0, 6100)
+    cfg = sim.pic_config_default(n=(5, 8, 8), L=(1.0, 1.0, 1.0), dt=0.1, ops=1)
+    with pytest.raises(sim.PicError):
+        sim.PicSim(cfg, x, v, q, m)
