@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--deterministic", action="store_true", help="bitwise reproducible mode")
     ap.add_argument("--ops", default="central2", choices=["central2", "spectral"],
                     help="spatial operators: central differences or the paper's spectral operators (FFT)")
     ap.add_argument("--shape-order", type=int, default=1, choices=[1, 2, 3],
@@ -279,7 +280,7 @@ def main():
 
     def timed(precision, with_clocks):
         """W warm-up steps, then K timed steps between barriers, CUDA events on the library's stream."""
-        extra = {"ops": 1 if args.ops == "spectral" else 0}
+        extra = {"ops": 1 if args.ops == "spectral" else 0, "deterministic": int(args.deterministic)}
         if args.shape_order > 1:
             extra.update(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
         cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
@@ -410,6 +411,7 @@ def main():
                                   f"{(3 * args.shape_order + 2) // 2}-point Gauss rule per piece"),
                        "shape_order": args.shape_order,
                        "ops": args.ops,
+                       "deterministic": bool(args.deterministic),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": f"inputs larger than L2 (FP64 particle state {w.n_particles * 120 / 1e9:.1f} GB "
                              f"per GPU: x, v, P, v^(n-1), iterate)",
