@@ -577,6 +577,45 @@ __device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3
 //              The next iterate is G(v^p); with p.accel, creeping particles are instead
 //              appended to a list and solved locally by k_local (which also scatters them);
 //   (commit)   x^{n+1}, P^{n+1}, v^{n+1} and (optionally) the particle diagnostics.
+// Orbit-piece classes for ordering the particles of a chunk: 1, 2, 3, >= 4 pieces, and a
+// last class for the threads past the end of the particle array.
+constexpr int PIECE_CLASSES = 5;
+
+// Estimated number of pieces of particle j's orbit under the iterate (1 + knots crossed), in
+// FP32: only the order of the work depends on it, never a result.
+__device__ __forceinline__ int piece_class(const StepParams& p, const double* __restrict__ xi,
+                                           const double* __restrict__ v, const double* __restrict__ vit, int64_t j) {
+    const int64_t np = p.np;
+    int pieces = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x0 = (float)(xi[a * np + j] - p.koff);
+        const float b = (float)(p.dt * 0.5 * (vit[a * np + j] + v[a * np + j]) * p.invH[a]);
+        pieces += abs((int)floorf(x0 + b) - (int)floorf(x0));
+    }
+    return min(pieces, PIECE_CLASSES - 1) - 1;
+}
+
+// Position of this thread's item in the block when items are ordered by class (stable: equal
+// classes keep the thread order).  Uses wcount as scratch; ends with a barrier.
+__device__ __forceinline__ int stable_class_rank(int cls, int (*wcount)[PIECE_CLASSES]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned mine = 0;
+#pragma unroll
+    for (int c = 0; c < PIECE_CLASSES; ++c) {
+        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+        if (lane == 0) wcount[w][c] = __popc(m);
+        if (cls == c) mine = m;
+    }
+    __syncthreads();
+    int pos = __popc(mine & ((1u << lane) - 1u));
+    for (int c = 0; c < cls; ++c)
+        for (int v = 0; v < nw; ++v) pos += wcount[v][c];
+    for (int v = 0; v < w; ++v) pos += wcount[v][cls];
+    __syncthreads();
+    return pos;
+}
+
 template <int QUAD, bool COMMIT, bool DIAG>
 __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __restrict__ xi,
                                                   const double* __restrict__ v, const double* __restrict__ P,
@@ -591,81 +630,98 @@ __global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __
     const int64_t np = p.np;
     double ev_num = 0.0, ev_den = 0.0, pieces_push = 0.0, pieces_scatter = 0.0;
     double k1 = 0.0, pwork = 0.0, ra_sq = 0.0, ra_max = 0.0, pu_max = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
-        double x0[3], vn[3], vi[3], Pn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x0[a] = xi[a * np + i];
-            vn[a] = v[a * np + i];
-            vi[a] = vit[a * np + i];
-            Pn[a] = P[a * np + i];
+    __shared__ int order[THREADS];
+    __shared__ int wcount[THREADS / 32][PIECE_CLASSES];
+    const int64_t nchunks = (np + THREADS - 1) / THREADS;
+    // Chunks of THREADS consecutive particles; inside a chunk the particles are handed to the
+    // threads in order of their (estimated) number of orbit pieces, so that the lanes of a
+    // warp run the same number of piece iterations (a stable ordering: deterministic).
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = ch * THREADS;
+        {
+            const int64_t j = base + threadIdx.x;
+            const int cls = j < np ? piece_class(p, xi, v, vit, j) : PIECE_CLASSES - 1;
+            order[stable_class_rank(cls, wcount)] = threadIdx.x;
         }
-        PushAcc acc;
-        PushOut o;
-        push_eval<QUAD, DIAG>(p, x0, vn, Pn, vi, table, acc, o);
-        if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
-        pieces_push += (double)o.nseg;
-        if (!(isfinite(o.vw[0]) && isfinite(o.vw[1]) && isfinite(o.vw[2]))) atomicOr(status, DEV_ERR_NONFINITE);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
-        if constexpr (!COMMIT) {
-            double beta_it[3], wv[3], bet2[3], dnum = 0.0, dden = 0.0;
+        __syncthreads();
+        const int64_t i = base + order[threadIdx.x];
+        if (i < np) {
+            double x0[3], vn[3], vi[3], Pn[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double d = o.vw[a] - vi[a];   // change of the iterate, v^{p+1} - v^p
-                dnum += d * d;
-                dden += o.vw[a] * o.vw[a];
-                beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
-                double vb2 = 0.5 * (o.vw[a] + vn[a]);
-                bet2[a] = p.dt * vb2 * p.invH[a];
-                wv[a] = p.q_dV * vb2;
+                x0[a] = xi[a * np + i];
+                vn[a] = v[a * np + i];
+                vi[a] = vit[a * np + i];
+                Pn[a] = P[a * np + i];
             }
-            const double xk[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};   // knot lattice
-            const bool creep = p.accel && is_creeping(xk, beta_it);
-            if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
-            if (creep) {
-                if (!creep_flag) {
-                    int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
-                    creep_list[k] = (int32_t)i;
-                }
-            } else {
-                ev_num += dnum;
-                ev_den += dden;
-                int ns = scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext);
-                if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
-                pieces_scatter += (double)ns;
-            }
-        } else {
-            // components sliding onto a knot (set by k_local): the orbit lands on the knot,
-            // v^{n+1}_a is the iterate itself and P_a follows from v = (P - q A_h(x)) / m
-            const uint8_t sb = slide ? slide[i] : 0;
+            PushAcc acc;
+            PushOut o;
+            push_eval<QUAD, DIAG>(p, x0, vn, Pn, vi, table, acc, o);
+            if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+            pieces_push += (double)o.nseg;
+            if (!(isfinite(o.vw[0]) && isfinite(o.vw[1]) && isfinite(o.vw[2]))) atomicOr(status, DEV_ERR_NONFINITE);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (sb & (1u << a)) {
-                    o.vw[a] = vi[a];
-                    o.Pw[a] = p.mass * o.vw[a] + p.q * o.Ae[a];
-                    vnew[a * np + i] = o.vw[a];
-                }
-                xi_out[a * np + i] = o.xe[a];
-                P_out[a * np + i] = o.Pw[a];
-            }
-            if constexpr (DIAG) {
-                double As[3], vb[3];
-                point_gather3(p, x0, table, 0, As);                       // A_h^n(x^n)
-                double ra2 = 0.0;
+            for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
+            if constexpr (!COMMIT) {
+                double beta_it[3], wv[3], bet2[3], dnum = 0.0, dden = 0.0;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    vb[a] = 0.5 * (vi[a] + vn[a]);
-                    double ra = o.Ae[a] - As[a] - p.dt * (acc.Ubar[a] + acc.DAv[a]);   // Eq. (RA-test)
-                    ra2 += ra * ra;
-                    ra_max = fmax(ra_max, fabs(ra));
-                    pwork += p.q * vb[a] * (-acc.gphi[a] - acc.Ubar[a]);                // q vbar . Ebar
-                    k1 += 0.5 * p.mass * o.vw[a] * o.vw[a];
+                    double d = o.vw[a] - vi[a];   // change of the iterate, v^{p+1} - v^p
+                    dnum += d * d;
+                    dden += o.vw[a] * o.vw[a];
+                    beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
+                    double vb2 = 0.5 * (o.vw[a] + vn[a]);
+                    bet2[a] = p.dt * vb2 * p.invH[a];
+                    wv[a] = p.q_dV * vb2;
                 }
-                ra_sq += ra2;
-                pu_max = fmax(pu_max, fabs(acc.pu - 1.0));
+                const double xk[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};   // knot lattice
+                const bool creep = p.accel && is_creeping(xk, beta_it);
+                if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
+                if (creep) {
+                    if (!creep_flag) {
+                        int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
+                        creep_list[k] = (int32_t)i;
+                    }
+                } else {
+                    ev_num += dnum;
+                    ev_den += dden;
+                    int ns = scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext);
+                    if (ns < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+                    pieces_scatter += (double)ns;
+                }
+            } else {
+                // components sliding onto a knot (set by k_local): the orbit lands on the knot,
+                // v^{n+1}_a is the iterate itself and P_a follows from v = (P - q A_h(x)) / m
+                const uint8_t sb = slide ? slide[i] : 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (sb & (1u << a)) {
+                        o.vw[a] = vi[a];
+                        o.Pw[a] = p.mass * o.vw[a] + p.q * o.Ae[a];
+                        vnew[a * np + i] = o.vw[a];
+                    }
+                    xi_out[a * np + i] = o.xe[a];
+                    P_out[a * np + i] = o.Pw[a];
+                }
+                if constexpr (DIAG) {
+                    double As[3], vb[3];
+                    point_gather3(p, x0, table, 0, As);                       // A_h^n(x^n)
+                    double ra2 = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vb[a] = 0.5 * (vi[a] + vn[a]);
+                        double ra = o.Ae[a] - As[a] - p.dt * (acc.Ubar[a] + acc.DAv[a]);   // Eq. (RA-test)
+                        ra2 += ra * ra;
+                        ra_max = fmax(ra_max, fabs(ra));
+                        pwork += p.q * vb[a] * (-acc.gphi[a] - acc.Ubar[a]);                // q vbar . Ebar
+                        k1 += 0.5 * p.mass * o.vw[a] * o.vw[a];
+                    }
+                    ra_sq += ra2;
+                    pu_max = fmax(pu_max, fabs(acc.pu - 1.0));
+                }
             }
         }
+        __syncthreads();   // order[] is rewritten by the next chunk
     }
     if constexpr (!COMMIT) {
         write_partial<double>(partials, S_EV_NUM, ev_num, sm, false);
