@@ -9,6 +9,8 @@
 // gives, with a = kappa^2 dt^2 / 4,
 //     (I - a Delta_h) phi^{n+1} = (I + a Delta_h) phi^n + dt psi^n + (dt^2 kappa^2 sigma1 / 2) rho^{n+1/2},
 // and the same for each component of A with (U, sigma2, J^{n+1/2}).
+#include <cooperative_groups.h>
+
 #include "pic_internal.h"
 
 namespace pic {
@@ -144,6 +146,35 @@ __global__ void k_cheb(MeshParams p, const double* __restrict__ x, double* __res
 
 // psi^{n+1} = 2 (phi^{n+1} - phi^n) / dt - psi^n (and U from A), then the gather table:
 // A^n, A^{n+1}, grad_h phi^{n+1/2}, U^{n+1/2}.
+// All `iters` Chebyshev steps of launch_helmholtz in one cooperative launch: the same
+// element-wise update as k_cheb on every field, with a grid-wide barrier between steps
+// (step k reads xa for even k and xb for odd k and writes the other), so the results are
+// those of the step-by-step launches, without a launch per step.
+__global__ void __launch_bounds__(THREADS) k_cheb_all(MeshParams p, double* xa, double* xb, double* __restrict__ d,
+                                                      const double* __restrict__ bvec, double c_id, double c_lap,
+                                                      int nfields, int iters, const double* __restrict__ alpha,
+                                                      const double* __restrict__ beta) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int64_t N = p.m.ncell, total = (int64_t)nfields * N;
+    for (int k = 0; k < iters; ++k) {
+        const double* x = (k & 1) ? xb : xa;
+        double* xo = (k & 1) ? xa : xb;
+        const double al = alpha[k], be = beta[k];
+        for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+             idx += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t f = idx / N, g = idx - f * N, off = f * N;
+            const double* xf = x + off;
+            Nb b = decompose(g, p.m);
+            double Hx = c_id * xf[g] - c_lap * lap(xf, b, p.m, p.invH);
+            double r = bvec[off + g] - Hx;
+            double dn = (al == 0.0 ? 0.0 : al * d[off + g]) + be * r;
+            d[off + g] = dn;
+            xo[off + g] = xf[g] + dn;
+        }
+        grid.sync();
+    }
+}
+
 __global__ void k_backsub_table(MeshParams p, const double* __restrict__ F0, const double* __restrict__ W0,
                                 const double* __restrict__ F1, double* __restrict__ W1, double* __restrict__ table) {
     const int64_t N = p.m.ncell;
@@ -325,6 +356,39 @@ void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nf
         ++c.launches;
         std::swap(*x_io, *x_spare);
     }
+}
+
+// The CN Helmholtz solve of a mesh phase: one cooperative launch when the device allows
+// it (the step coefficients are in device memory), else one launch per step.
+void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare) {
+    const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
+    if (c.cheb_coop_blocks <= 0 || !c.cheb_coef_dev) {
+        launch_helmholtz(c, c.rhs, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, x_io, x_spare);
+        return;
+    }
+    MeshParams p = mesh_params(c);
+    double* xa = *x_io;
+    double* xb = *x_spare;
+    const double* bvec = c.rhs;
+    double c_id = 1.0, c_lap = a;
+    int nf = 4, iters = c.cheb_iters;
+    const double* al = c.cheb_coef_dev;
+    const double* be = c.cheb_coef_dev + 1024;
+    void* args[] = {&p, &xa, &xb, &c.cheb_d, &bvec, &c_id, &c_lap, &nf, &iters, &al, &be};
+    const int64_t want = (4 * c.m.ncell + THREADS - 1) / THREADS;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, c.cheb_coop_blocks));
+    cudaLaunchCooperativeKernel((const void*)k_cheb_all, dim3(grid), dim3(THREADS), args, 0, c.stream);
+    ++c.launches;
+    if (iters & 1) std::swap(*x_io, *x_spare);
+}
+
+// Co-resident blocks of k_cheb_all on the device (0: no cooperative launch).
+int cheb_coop_capacity(const Ctx& c) {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_all, THREADS, 0) != cudaSuccess) return 0;
+    return per_sm * c.sms;
 }
 
 void launch_backsub_table(Ctx& c, bool) {

@@ -276,6 +276,12 @@ pic_status allocate(pic_ctx* ctx) {
     ALLOC(c.W1, double, 4 * N);
     ALLOC(c.rho1, double, N);
     ALLOC(c.cheb_d, double, 4 * N);
+    ALLOC(c.cheb_coef_dev, double, 2048);
+    cudaMemcpyAsync(c.cheb_coef_dev, c.cheb_alpha, sizeof(double) * 1024, cudaMemcpyHostToDevice, c.stream);
+    cudaMemcpyAsync(c.cheb_coef_dev + 1024, c.cheb_beta, sizeof(double) * 1024, cudaMemcpyHostToDevice, c.stream);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "chebyshev coefficients");
+    c.cheb_coop_blocks = cheb_coop_capacity(c);
+    cudaGetLastError();
     ALLOC(c.rhs0, double, 4 * N);
     ALLOC(c.rhs, double, 4 * N);
     for (int k = 0; k < 3; ++k) ALLOC(c.J[k], double, 3 * N);
@@ -406,14 +412,13 @@ void mesh_begin(Ctx& c) {
 // The mesh half of one Algorithm 1 iteration: continuity, CN solve (warm-started from F1),
 // back-substitution and the gather table.
 void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev) {
-    const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
     ProfScope ps(c, PH_MESH);
     if (c.cfg.ops == PIC_OPS_SPECTRAL) {
         launch_spec_mesh_phase(c, Jcur, Jprev);
         return;
     }
     launch_source(c, Jcur, Jprev);
-    launch_helmholtz(c, c.rhs, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, &c.F1, &c.F1b);
+    launch_helmholtz_cn(c, &c.F1, &c.F1b);
     launch_backsub_table(c, false);
 }
 

@@ -150,6 +150,8 @@ struct Ctx {
     // Chebyshev schedule for the CN Helmholtz solve
     int cheb_iters = 0;
     double cheb_alpha[1024], cheb_beta[1024];
+    double* cheb_coef_dev = nullptr;   // alpha (1024) | beta (1024) on the device, for k_cheb_all
+    int cheb_coop_blocks = 0;          // co-resident blocks for the cooperative solve (0: none)
 
     // live profiling: event pairs per phase, resolved at the next stream synchronisation
     bool prof = false;
@@ -204,6 +206,8 @@ void launch_source(Ctx& c, const double* Jcur, const double* Jprev);
 void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nfields, int iters,
                       const double* alpha, const double* beta, double** x_io, double** x_spare);
 void launch_backsub_table(Ctx& c, bool diag);
+void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare);
+int cheb_coop_capacity(const Ctx& c);
 void launch_null_project(Ctx& c, double* f, double add_const);
 void launch_mesh_energy(Ctx& c, const double* F, const double* W, int slot);
 void launch_mesh_diag(Ctx& c, const double* Jfinal);
