@@ -49,7 +49,7 @@ FLOPS_PER_PUSH_PIECE = 409
 FLOPS_PER_SCATTER_PIECE = 150
 # DRAM bytes (read + write) of one k_push launch on the 32^3 x 2.1M workload, from the ncu
 # capture summarised in profiles/k_push_fp64_twostream-32c-2M.md (this kernel version).
-KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 241.8e6}
+KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 244.4e6}
 
 
 def parse():

@@ -616,8 +616,11 @@ __device__ __forceinline__ int stable_class_rank(int cls, int (*wcount)[PIECE_CL
     return pos;
 }
 
+// Two resident blocks per SM (at most 128 registers, a few spills) hide more of the FP64
+// pipe's latency than one block at 178 registers (measured: 5% less push time at 32^3); the
+// diagnostics variant keeps one block, its larger state would spill far more.
 template <int QUAD, bool COMMIT, bool DIAG>
-__global__ void __launch_bounds__(THREADS) k_push(StepParams p, const double* __restrict__ xi,
+__global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, const double* __restrict__ xi,
                                                   const double* __restrict__ v, const double* __restrict__ P,
                                                   const double* __restrict__ vit, const double* __restrict__ table,
                                                   double* __restrict__ vnew, double* __restrict__ Jnext,
