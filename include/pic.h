@@ -84,7 +84,10 @@ typedef struct {
                                      with the iteration's fields fixed (an accelerated fixed point,
                                      §4.8); all others, and every particle when 0, take the plain
                                      update v^{p+1} = G(v^p) of Algorithm 1 */
-    double helmholtz_tol;         /* target error reduction of the CN Helmholtz solve (Chebyshev) */
+    double helmholtz_tol;         /* accuracy of the CN Helmholtz solve (Chebyshev, central2): each
+                                     mesh phase runs the fewest steps whose error bound is below
+                                     helmholtz_tol times the solution's norm, from the warm start's
+                                     residual (at most the schedule that reduces any start by it) */
     double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v <= this */
     int32_t mixed_max32;          /* PIC_MIXED: at most this many FP32 iterations per step */
     int32_t deterministic;        /* 1: bitwise reproducible steps.  The particle sort is a stable

@@ -146,17 +146,30 @@ __global__ void k_cheb(MeshParams p, const double* __restrict__ x, double* __res
 
 // psi^{n+1} = 2 (phi^{n+1} - phi^n) / dt - psi^n (and U from A), then the gather table:
 // A^n, A^{n+1}, grad_h phi^{n+1/2}, U^{n+1/2}.
-// All `iters` Chebyshev steps of launch_helmholtz in one cooperative launch: the same
-// element-wise update as k_cheb on every field, with a grid-wide barrier between steps
-// (step k reads xa for even k and xb for odd k and writes the other), so the results are
-// those of the step-by-step launches, without a launch per step.
+// The Chebyshev steps of a CN mesh phase in one cooperative launch: the same element-wise
+// update as k_cheb on every field, with a grid-wide barrier between steps (step k reads xa for
+// even k and xb for odd k and writes the other).
+//
+// Step count.  The operator I - a Delta_h has spectrum in [1, lmax], so the initial error of
+// field f obeys |e_0| <= |r_0| (r_0 = b - A x_0, the warm start's residual) and after K steps
+// |e_K| <= 2 rho^K |r_0|, rho = (sqrt(lmax) - 1) / (sqrt(lmax) + 1); the solution obeys
+// |x| >= |b| / lmax.  Step 0 measures |r_0,f| and |b_f| (a grid reduction in a fixed order,
+// so every block takes the same decision) and the solve stops after the smallest K with
+// 2 rho^K |r_0,f| lmax <= tol |b_f| for every field, rounded up to the parity of the full
+// schedule (so the result lands in the same buffer) and at most `iters`.  A warm start that is
+// already close, as in the later Picard iterations, needs far fewer steps than the schedule.
 __global__ void __launch_bounds__(THREADS) k_cheb_all(MeshParams p, double* xa, double* xb, double* __restrict__ d,
                                                       const double* __restrict__ bvec, double c_id, double c_lap,
                                                       int nfields, int iters, const double* __restrict__ alpha,
-                                                      const double* __restrict__ beta) {
+                                                      const double* __restrict__ beta, double* __restrict__ red,
+                                                      double lmax, double rate, double tol) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    __shared__ double sm[32];
+    __shared__ int sK;
     const int64_t N = p.m.ncell, total = (int64_t)nfields * N;
-    for (int k = 0; k < iters; ++k) {
+    double r2[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
+    int K = iters;
+    for (int k = 0; k < K; ++k) {
         const double* x = (k & 1) ? xb : xa;
         double* xo = (k & 1) ? xa : xb;
         const double al = alpha[k], be = beta[k];
@@ -166,12 +179,61 @@ __global__ void __launch_bounds__(THREADS) k_cheb_all(MeshParams p, double* xa, 
             const double* xf = x + off;
             Nb b = decompose(g, p.m);
             double Hx = c_id * xf[g] - c_lap * lap(xf, b, p.m, p.invH);
-            double r = bvec[off + g] - Hx;
+            const double bv = bvec[off + g];
+            double r = bv - Hx;
+            if (k == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    r2[q] += q == f ? r * r : 0.0;
+                    b2[q] += q == f ? bv * bv : 0.0;
+                }
+            }
             double dn = (al == 0.0 ? 0.0 : al * d[off + g]) + be * r;
             d[off + g] = dn;
             xo[off + g] = xf[g] + dn;
         }
+        if (k == 0 && rate > 0.0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double sr = block_sum(r2[q], sm);
+                const double sb = block_sum(b2[q], sm);
+                if (threadIdx.x == 0) {
+                    red[blockIdx.x * 8 + q] = sr;
+                    red[blockIdx.x * 8 + 4 + q] = sb;
+                }
+            }
+        }
         grid.sync();
+        if (k == 0 && rate > 0.0) {
+            // every block sums the per-block partials the same way: thread t takes blocks
+            // t, t + blockDim, ..., then a fixed-order block sum
+            double tot[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                double v = 0.0;
+                for (unsigned blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) v += red[blk * 8 + q];
+                tot[q] = block_sum(v, sm);
+            }
+            if (threadIdx.x == 0) {
+                int need = 1;
+                for (int q = 0; q < nfields; ++q) {
+                    const double sr = tot[q], sb = tot[4 + q];
+                    int kq;
+                    if (sr == 0.0) kq = 1;
+                    else if (sb == 0.0) kq = iters;
+                    else {
+                        const double ratio = 2.0 * sqrt(sr) * lmax / (tol * sqrt(sb));
+                        kq = ratio <= 1.0 ? 1 : (int)ceil(log(ratio) * rate);
+                    }
+                    need = max(need, kq);
+                }
+                need = min(need, iters);
+                if ((need & 1) != (iters & 1)) need = min(need + 1, iters);
+                sK = need;
+            }
+            __syncthreads();
+            K = sK;
+        }
     }
 }
 
@@ -374,7 +436,9 @@ void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare) {
     int nf = 4, iters = c.cheb_iters;
     const double* al = c.cheb_coef_dev;
     const double* be = c.cheb_coef_dev + 1024;
-    void* args[] = {&p, &xa, &xb, &c.cheb_d, &bvec, &c_id, &c_lap, &nf, &iters, &al, &be};
+    double lmax = c.cheb_lmax, rate = c.cheb_rate, tol = c.cfg.helmholtz_tol;
+    void* args[] = {&p, &xa, &xb, &c.cheb_d, &bvec, &c_id, &c_lap, &nf, &iters, &al, &be, &c.cheb_red, &lmax, &rate,
+                    &tol};
     const int64_t want = (4 * c.m.ncell + THREADS - 1) / THREADS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, c.cheb_coop_blocks));
     cudaLaunchCooperativeKernel((const void*)k_cheb_all, dim3(grid), dim3(THREADS), args, 0, c.stream);

@@ -494,6 +494,56 @@ __global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, dou
     }
 }
 
+// Orbit-piece classes for ordering the particles of a chunk: 1, 2, 3, >= 4 pieces, and a
+// last class for the threads past the end of the particle array.
+constexpr int PIECE_CLASSES = 5;
+
+// Estimated number of pieces of an orbit x0 + s beta (1 + knots crossed), in FP32: only the
+// order of the work depends on it, never a result.
+__device__ __forceinline__ int piece_class_of(const StepParams& p, const double x0[3], const double beta[3]) {
+    int pieces = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = (float)(x0[a] - p.koff);
+        const float b = (float)beta[a];
+        pieces += abs((int)floorf(x + b) - (int)floorf(x));
+    }
+    return min(pieces, PIECE_CLASSES - 1) - 1;
+}
+
+// The same for particle j under the iterate vit.
+__device__ __forceinline__ int piece_class(const StepParams& p, const double* __restrict__ xi,
+                                           const double* __restrict__ v, const double* __restrict__ vit, int64_t j) {
+    const int64_t np = p.np;
+    double x0[3], beta[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x0[a] = xi[a * np + j];
+        beta[a] = p.dt * 0.5 * (vit[a * np + j] + v[a * np + j]) * p.invH[a];
+    }
+    return piece_class_of(p, x0, beta);
+}
+
+// Position of this thread's item in the block when items are ordered by class (stable: equal
+// classes keep the thread order).  Uses wcount as scratch; ends with a barrier.
+__device__ __forceinline__ int stable_class_rank(int cls, int (*wcount)[PIECE_CLASSES]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned mine = 0;
+#pragma unroll
+    for (int c = 0; c < PIECE_CLASSES; ++c) {
+        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+        if (lane == 0) wcount[w][c] = __popc(m);
+        if (cls == c) mine = m;
+    }
+    __syncthreads();
+    int pos = __popc(mine & ((1u << lane) - 1u));
+    for (int c = 0; c < cls; ++c)
+        for (int v = 0; v < nw; ++v) pos += wcount[v][c];
+    for (int v = 0; v < w; ++v) pos += wcount[v][cls];
+    __syncthreads();
+    return pos;
+}
+
 // v^{n+1,0} = 2 v^n - v^{n-1} (Algorithm 1, extrapolated start) unless an iterate is given;
 // then the orbit current of that iterate, and sum_i |v^n_i| for the e_J floor.
 template <int QUAD>
@@ -502,22 +552,44 @@ __global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, con
                                 double* __restrict__ vit, double* __restrict__ J, double* __restrict__ partials,
                                 int* __restrict__ status) {
     __shared__ double sm[32];
-    const int64_t np = p.np;
+    __shared__ int order[THREADS];
+    __shared__ int wcount[THREADS / 32][PIECE_CLASSES];
+    const int64_t np = p.np, nchunks = (np + THREADS - 1) / THREADS;
     double jsc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    // chunks of THREADS particles handed to the threads by orbit-piece count (as in k_push)
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = ch * THREADS;
         double x0[3], vn[3], vi[3], beta[3], w[3];
+        int cls = PIECE_CLASSES - 1;
+        if (base + threadIdx.x < np) {
+            const int64_t j = base + threadIdx.x;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x0[a] = xi[a * np + i];
-            vn[a] = v[a * np + i];
-            vi[a] = vgiven ? vgiven[a * np + i] : 2.0 * vn[a] - vprev[a * np + i];
-            vit[a * np + i] = vi[a];
-            double vb = 0.5 * (vi[a] + vn[a]);
-            beta[a] = p.dt * vb * p.invH[a];
-            w[a] = p.q_dV * vb;
+            for (int a = 0; a < 3; ++a) {
+                x0[a] = xi[a * np + j];
+                vn[a] = v[a * np + j];
+                vi[a] = vgiven ? vgiven[a * np + j] : 2.0 * vn[a] - vprev[a * np + j];
+                vit[a * np + j] = vi[a];
+                beta[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
+            }
+            jsc += sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+            cls = piece_class_of(p, x0, beta);
         }
-        jsc += sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
-        if (scatter_orbit<QUAD>(p, x0, beta, w, J) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        order[stable_class_rank(cls, wcount)] = threadIdx.x;
+        __syncthreads();
+        const int64_t i = base + order[threadIdx.x];
+        if (i < np) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x0[a] = xi[a * np + i];
+                vn[a] = v[a * np + i];
+                vi[a] = vgiven ? vgiven[a * np + i] : 2.0 * vn[a] - vprev[a * np + i];
+                const double vb = 0.5 * (vi[a] + vn[a]);
+                beta[a] = p.dt * vb * p.invH[a];
+                w[a] = p.q_dV * vb;
+            }
+            if (scatter_orbit<QUAD>(p, x0, beta, w, J) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        }
+        __syncthreads();   // order[] is rewritten by the next chunk
     }
     write_partial<double>(partials, S_JSCALE, jsc, sm, false);
 }
@@ -577,45 +649,6 @@ __device__ __forceinline__ void push_eval(const StepParams& p, const double x0[3
 //              The next iterate is G(v^p); with p.accel, creeping particles are instead
 //              appended to a list and solved locally by k_local (which also scatters them);
 //   (commit)   x^{n+1}, P^{n+1}, v^{n+1} and (optionally) the particle diagnostics.
-// Orbit-piece classes for ordering the particles of a chunk: 1, 2, 3, >= 4 pieces, and a
-// last class for the threads past the end of the particle array.
-constexpr int PIECE_CLASSES = 5;
-
-// Estimated number of pieces of particle j's orbit under the iterate (1 + knots crossed), in
-// FP32: only the order of the work depends on it, never a result.
-__device__ __forceinline__ int piece_class(const StepParams& p, const double* __restrict__ xi,
-                                           const double* __restrict__ v, const double* __restrict__ vit, int64_t j) {
-    const int64_t np = p.np;
-    int pieces = 1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float x0 = (float)(xi[a * np + j] - p.koff);
-        const float b = (float)(p.dt * 0.5 * (vit[a * np + j] + v[a * np + j]) * p.invH[a]);
-        pieces += abs((int)floorf(x0 + b) - (int)floorf(x0));
-    }
-    return min(pieces, PIECE_CLASSES - 1) - 1;
-}
-
-// Position of this thread's item in the block when items are ordered by class (stable: equal
-// classes keep the thread order).  Uses wcount as scratch; ends with a barrier.
-__device__ __forceinline__ int stable_class_rank(int cls, int (*wcount)[PIECE_CLASSES]) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned mine = 0;
-#pragma unroll
-    for (int c = 0; c < PIECE_CLASSES; ++c) {
-        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
-        if (lane == 0) wcount[w][c] = __popc(m);
-        if (cls == c) mine = m;
-    }
-    __syncthreads();
-    int pos = __popc(mine & ((1u << lane) - 1u));
-    for (int c = 0; c < cls; ++c)
-        for (int v = 0; v < nw; ++v) pos += wcount[v][c];
-    for (int v = 0; v < w; ++v) pos += wcount[v][cls];
-    __syncthreads();
-    return pos;
-}
-
 // Two resident blocks per SM (at most 128 registers, a few spills) hide more of the FP64
 // pipe's latency than one block at 178 registers (measured: 5% less push time at 32^3); the
 // diagnostics variant keeps one block, its larger state would spill far more.

@@ -237,6 +237,9 @@ void setup_geometry(Ctx& c) {
         lmax += a * mx * c.invH[ax] * c.invH[ax];
     }
     c.cheb_iters = cheb_schedule(1.0, lmax, c.cfg.helmholtz_tol, c.cheb_alpha, c.cheb_beta, 1024);
+    c.cheb_lmax = lmax;
+    const double rho = (std::sqrt(lmax) - 1.0) / (std::sqrt(lmax) + 1.0);
+    c.cheb_rate = (c.cheb_iters > 1 && rho > 0.0) ? 1.0 / std::log(1.0 / rho) : 0.0;
 }
 
 #define ALLOC(ptr, type, count)                                                          \
@@ -282,6 +285,7 @@ pic_status allocate(pic_ctx* ctx) {
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "chebyshev coefficients");
     c.cheb_coop_blocks = cheb_coop_capacity(c);
     cudaGetLastError();
+    ALLOC(c.cheb_red, double, 8 * (int64_t)std::max(1, c.cheb_coop_blocks));
     ALLOC(c.rhs0, double, 4 * N);
     ALLOC(c.rhs, double, 4 * N);
     for (int k = 0; k < 3; ++k) ALLOC(c.J[k], double, 3 * N);

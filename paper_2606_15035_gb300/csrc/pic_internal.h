@@ -152,6 +152,9 @@ struct Ctx {
     double cheb_alpha[1024], cheb_beta[1024];
     double* cheb_coef_dev = nullptr;   // alpha (1024) | beta (1024) on the device, for k_cheb_all
     int cheb_coop_blocks = 0;          // co-resident blocks for the cooperative solve (0: none)
+    double cheb_lmax = 1.0;            // largest eigenvalue of I - a Delta_h
+    double cheb_rate = 0.0;            // 1 / log(1 / rho) of the Chebyshev bound (0: one step)
+    double* cheb_red = nullptr;        // per-block sums of the cooperative solve (8 per block)
 
     // live profiling: event pairs per phase, resolved at the next stream synchronisation
     bool prof = false;
