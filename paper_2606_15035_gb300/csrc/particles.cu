@@ -797,114 +797,172 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                                                    double* __restrict__ Jnext, const int32_t* __restrict__ creep_list,
                                                    const int* __restrict__ creep_count,
                                                    const uint8_t* __restrict__ creep_flag, uint8_t* __restrict__ slide,
-                                                   double* __restrict__ partials, int* __restrict__ status) {
+                                                   int* __restrict__ queue_head, double* __restrict__ partials,
+                                                   int* __restrict__ status) {
     __shared__ double sm[32];
     const int64_t np = p.np;
-    // the creeping particles: a list in arrival order, or (deterministic mode) flags in index order
+    // The creeping particles: a list in arrival order, taken from a shared queue by whichever
+    // lane is free; or (deterministic mode) flags in index order, each thread walking its own
+    // fixed stride, so that the assignment (and every partial sum) is reproducible.
     const int64_t count = creep_flag ? np : (int64_t)*creep_count;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    int64_t next_static = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double ev_num = 0.0, ev_den = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
-        if (creep_flag && !creep_flag[k]) continue;
-        const int64_t i = creep_flag ? k : (int64_t)creep_list[k];
-        double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
-        double ua[3], ga[3], ub[3], gb[3], side[3], fac[3];
-        bool brk[3], secok[3];
-        double nrm = 0.0;
+    // One particle's solve is a sequence of push evaluations: sliding probes (phase 0: just
+    // short of the knot, phase 1: just past it, per probed axis), the first evaluation
+    // (phase 2), then up to LOCAL_STEPS - 1 iteration steps (phase 3).  Every round, each lane
+    // with a particle makes its next evaluation together with the others, and a lane whose
+    // particle is done takes a new one: the warp's evaluations stay full even when particles
+    // need very different numbers of them.
+    bool active = false, exhausted = false;
+    int64_t i = 0;
+    int phase = 0, paxis = 0, nstep = 0;
+    double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
+    double ua[3], ga[3], ub[3], gb[3], side[3], fac[3], uland[3], dk[3], ue[3];
+    bool brk[3], secok[3], sl[3], probe[3];
+    double tol = 0.0, gm = 0.0;
+    while (true) {
+        if (!active && !exhausted) {
+            int64_t k = -1;
+            if (creep_flag) {
+                while (next_static < count && !creep_flag[next_static]) next_static += T;
+                if (next_static < count) {
+                    k = next_static;
+                    next_static += T;
+                }
+            } else {
+                const int q = atomicAdd(queue_head, 1);
+                k = q < count ? q : -1;
+            }
+            if (k < 0) {
+                exhausted = true;
+            } else {
+                i = creep_flag ? k : (int64_t)creep_list[k];
+                double nrm = 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x0[a] = xi[a * np + i];
-            vn[a] = v[a * np + i];
-            Pn[a] = P[a * np + i];
-            u0[a] = vit[a * np + i];
-            u1[a] = vnew[a * np + i];          // G(v^p) from k_push
-            gsave[a * np + i] = u1[a];
-            r0[a] = u1[a] - u0[a];
-            nrm += u0[a] * u0[a];
-        }
-        const double tol = LOCAL_TOL * fmax(sqrt(nrm), 1e-300);
-        PushAcc acc;
-        PushOut o;
-        // Sliding probes: a component starting within D_KNOT of a knot is tested just short of
-        // and just past landing on it (beta_a = d -+ SLIDE_PROBE); if both sides push onto the
-        // knot there is no root (G jumps there) and the component lands exactly on the knot.
-        bool sl[3] = {false, false, false};
-        double uland[3];
+                for (int a = 0; a < 3; ++a) {
+                    x0[a] = xi[a * np + i];
+                    vn[a] = v[a * np + i];
+                    Pn[a] = P[a * np + i];
+                    u0[a] = vit[a * np + i];
+                    u1[a] = vnew[a * np + i];          // G(v^p) from k_push
+                    gsave[a * np + i] = u1[a];
+                    r0[a] = u1[a] - u0[a];
+                    nrm += u0[a] * u0[a];
+                    dk[a] = rint(x0[a] - p.koff) - (x0[a] - p.koff);   // signed distance to the nearest knot
+                    uland[a] = 2.0 * dk[a] * p.H[a] / p.dt - vn[a];
+                    sl[a] = (slide[i] >> a) & 1u;       // pinned earlier in this step: stays pinned
+                    probe[a] = !sl[a] && fabs(dk[a]) < D_KNOT;
+                }
+                tol = LOCAL_TOL * fmax(sqrt(nrm), 1e-300);
+                paxis = 0;
+                while (paxis < 3 && !probe[paxis]) ++paxis;
+                phase = paxis < 3 ? 0 : 2;
+                if (phase == 2) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double dk = rint(x0[a] - p.koff) - (x0[a] - p.koff);   // signed distance to the nearest knot
-            uland[a] = 2.0 * dk * p.H[a] / p.dt - vn[a];
-            if ((slide[i] >> a) & 1u) {
-                sl[a] = true;                            // pinned earlier in this step: stays pinned
-            } else if (fabs(dk) < D_KNOT) {
-                double um[3] = {u1[0], u1[1], u1[2]}, up[3] = {u1[0], u1[1], u1[2]};
-                um[a] = 2.0 * (dk - SLIDE_PROBE) * p.H[a] / p.dt - vn[a];
-                up[a] = 2.0 * (dk + SLIDE_PROBE) * p.H[a] / p.dt - vn[a];
-                push_eval<QUAD, false>(p, x0, vn, Pn, um, table, acc, o);
-                const double gm = o.vw[a] - um[a];
-                push_eval<QUAD, false>(p, x0, vn, Pn, up, table, acc, o);
-                const double gp = o.vw[a] - up[a];
-                sl[a] = gm > 0.0 && gp < 0.0;
+                    for (int a = 0; a < 3; ++a)
+                        if (sl[a]) u1[a] = uland[a];
+                }
+                nstep = 0;
+                active = true;
             }
         }
+        if (!__any_sync(0xffffffffu, active)) break;
+        // the evaluation point of this round
+        if (active) {
+            if (phase <= 1) {
+                // Sliding probes: a component starting within D_KNOT of a knot is tested just
+                // short of and just past landing on it (beta_a = d -+ SLIDE_PROBE); if both sides
+                // push onto the knot there is no root (G jumps there) and it lands on the knot.
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (sl[a]) u1[a] = uland[a];
-        push_eval<QUAD, false>(p, x0, vn, Pn, u1, table, acc, o);
-        if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+                for (int a = 0; a < 3; ++a) ue[a] = u1[a];
+                const double sg = phase == 0 ? -SLIDE_PROBE : SLIDE_PROBE;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            r1[a] = sl[a] ? 0.0 : o.vw[a] - u1[a];
-            if (sl[a]) r0[a] = 0.0;
-            const bool b1 = sl[a] || fabs(r1[a]) < fabs(r0[a]);
-            bu[a] = b1 ? u1[a] : u0[a];
-            br[a] = sl[a] ? 0.0 : (b1 ? fabs(r1[a]) : fabs(r0[a]));
-            brk[a] = !sl[a] && r0[a] * r1[a] < 0.0;
-            ua[a] = u0[a];
-            ga[a] = r0[a];
-            ub[a] = u1[a];
-            gb[a] = r1[a];
-            side[a] = 0.0;
-            secok[a] = fabs(r1[a]) <= 0.5 * fabs(r0[a]);
-            fac[a] = 2.0;
-        }
-        for (int step = 0; step < LOCAL_STEPS - 1; ++step) {
-            if (br[0] <= tol && br[1] <= tol && br[2] <= tol) break;
-            double u2[3];
+                for (int a = 0; a < 3; ++a)
+                    if (a == paxis) ue[a] = 2.0 * (dk[a] + sg) * p.H[a] / p.dt - vn[a];
+            } else if (phase == 2) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double fp = ub[a] - gb[a] * (ub[a] - ua[a]) / (gb[a] - ga[a]);
-                double sec = -(u1[a] - u0[a]) / (r1[a] - r0[a]);
-                sec = isfinite(sec) ? fmin(fmax(sec, -OMEGA_MAX), OMEGA_MAX) : 1.0;
-                if (sl[a]) {
-                    u2[a] = uland[a];                    // pinned: lands on the knot
-                } else if (brk[a] && isfinite(fp)) {
-                    u2[a] = fp;                          // Illinois inside the bracket
-                } else if (!brk[a] && !secok[a]) {
-                    u2[a] = u1[a] + fac[a] * r1[a];      // grow along g until g changes sign
-                    fac[a] *= 2.0;
-                } else {
-                    u2[a] = u1[a] + sec * r1[a];         // secant while it converges
+                for (int a = 0; a < 3; ++a) ue[a] = u1[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double fp = ub[a] - gb[a] * (ub[a] - ua[a]) / (gb[a] - ga[a]);
+                    double sec = -(u1[a] - u0[a]) / (r1[a] - r0[a]);
+                    sec = isfinite(sec) ? fmin(fmax(sec, -OMEGA_MAX), OMEGA_MAX) : 1.0;
+                    if (sl[a]) {
+                        ue[a] = uland[a];                    // pinned: lands on the knot
+                    } else if (brk[a] && isfinite(fp)) {
+                        ue[a] = fp;                          // Illinois inside the bracket
+                    } else if (!brk[a] && !secok[a]) {
+                        ue[a] = u1[a] + fac[a] * r1[a];      // grow along g until g changes sign
+                        fac[a] *= 2.0;
+                    } else {
+                        ue[a] = u1[a] + sec * r1[a];         // secant while it converges
+                    }
                 }
             }
-            push_eval<QUAD, false>(p, x0, vn, Pn, u2, table, acc, o);
-            if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        }
+        PushAcc acc;
+        PushOut o;
+        if (active) {
+            push_eval<QUAD, false>(p, x0, vn, Pn, ue, table, acc, o);
+            if (phase >= 2 && o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        }
+        if (!active) continue;
+        bool done = false;
+        if (phase == 0) {
+            gm = o.vw[paxis] - ue[paxis];
+            phase = 1;
+        } else if (phase == 1) {
+            const double gp = o.vw[paxis] - ue[paxis];
+            sl[paxis] = gm > 0.0 && gp < 0.0;
+            ++paxis;
+            while (paxis < 3 && !probe[paxis]) ++paxis;
+            if (paxis < 3) {
+                phase = 0;
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (sl[a]) u1[a] = uland[a];
+                phase = 2;
+            }
+        } else if (phase == 2) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const double r2 = sl[a] ? 0.0 : o.vw[a] - u2[a];
+                r1[a] = sl[a] ? 0.0 : o.vw[a] - u1[a];
+                if (sl[a]) r0[a] = 0.0;
+                const bool b1 = sl[a] || fabs(r1[a]) < fabs(r0[a]);
+                bu[a] = b1 ? u1[a] : u0[a];
+                br[a] = sl[a] ? 0.0 : (b1 ? fabs(r1[a]) : fabs(r0[a]));
+                brk[a] = !sl[a] && r0[a] * r1[a] < 0.0;
+                ua[a] = u0[a];
+                ga[a] = r0[a];
+                ub[a] = u1[a];
+                gb[a] = r1[a];
+                side[a] = 0.0;
+                secok[a] = fabs(r1[a]) <= 0.5 * fabs(r0[a]);
+                fac[a] = 2.0;
+            }
+            phase = 3;
+            done = nstep >= LOCAL_STEPS - 1 || (br[0] <= tol && br[1] <= tol && br[2] <= tol);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double r2 = sl[a] ? 0.0 : o.vw[a] - ue[a];
                 if (!sl[a] && fabs(r2) < br[a]) {
                     br[a] = fabs(r2);
-                    bu[a] = u2[a];
+                    bu[a] = ue[a];
                 }
                 secok[a] = secok[a] && fabs(r2) <= 0.5 * fabs(r1[a]);
                 if (brk[a]) {
                     if (r2 * gb[a] > 0.0) {            // replaces the b end
                         if (side[a] > 0.0) ga[a] *= 0.5;
-                        ub[a] = u2[a];
+                        ub[a] = ue[a];
                         gb[a] = r2;
                         side[a] = 1.0;
                     } else {                           // replaces the a end
                         if (side[a] < 0.0) gb[a] *= 0.5;
-                        ua[a] = u2[a];
+                        ua[a] = ue[a];
                         ga[a] = r2;
                         side[a] = -1.0;
                     }
@@ -912,15 +970,19 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                     brk[a] = true;
                     ua[a] = u1[a];
                     ga[a] = r1[a];
-                    ub[a] = u2[a];
+                    ub[a] = ue[a];
                     gb[a] = r2;
                 }
                 u0[a] = u1[a];
                 r0[a] = r1[a];
-                u1[a] = u2[a];
+                u1[a] = ue[a];
                 r1[a] = r2;
             }
+            ++nstep;
+            done = nstep >= LOCAL_STEPS - 1 || (br[0] <= tol && br[1] <= tol && br[2] <= tol);
         }
+        if (!done) continue;
+        // the particle's solve is over: its best iterate, sliding marks, e_v terms and current
         uint8_t sb = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -942,6 +1004,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
             wv[a] = p.q_dV * vb2;
         }
         if (scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        active = false;
     }
     write_partial<double>(partials, S_EVL_NUM, ev_num, sm, false);
     write_partial<double>(partials, S_EVL_DEN, ev_den, sm, false);
@@ -1221,7 +1284,7 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
     int nb = particle_blocks(c);
     const bool det = c.cfg.deterministic && !commit;
     const bool closed = c.cfg.quadrature == PIC_QUAD_CLOSED;
-    if (!commit) cudaMemsetAsync(c.creep_count, 0, sizeof(int), c.stream);
+    if (!commit) cudaMemsetAsync(c.creep_count, 0, 2 * sizeof(int), c.stream);   // count, k_local queue head
 #define PIC_PUSH(Q, C, D)                                                                                        \
     k_push<Q, C, D><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.xi_new, c.P_new, \
                                                   c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,  \
@@ -1244,11 +1307,11 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
         if (closed)
             k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
                                                      c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
-                                                     c.slide, c.partials, c.dev_status);
+                                                     c.slide, c.creep_count + 1, c.partials, c.dev_status);
         else
             k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
                                                      c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
-                                                     c.slide, c.partials, c.dev_status);
+                                                     c.slide, c.creep_count + 1, c.partials, c.dev_status);
         ++c.launches;
     }
     if (det && Jnext) launch_exact_finish(c, Jnext, 3 * c.m.ncell, c.inv_u_J);

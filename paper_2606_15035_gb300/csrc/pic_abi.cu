@@ -263,7 +263,7 @@ pic_status allocate(pic_ctx* ctx) {
     ALLOC(c.creep_list, int32_t, std::max<int64_t>(c.np, 1));
     ALLOC(c.gsave, double, np3);
     ALLOC(c.slide, uint8_t, std::max<int64_t>(c.np, 1));
-    ALLOC(c.creep_count, int, 1);
+    ALLOC(c.creep_count, int, 2);   // creeping count, queue head of the local solves
     ALLOC(c.id, int64_t, std::max<int64_t>(c.np, 1));
     ALLOC(c.id_tmp, int64_t, std::max<int64_t>(c.np, 1));
     ALLOC(c.key, int32_t, std::max<int64_t>(c.np, 1));
