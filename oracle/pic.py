@@ -243,7 +243,7 @@ def creeping(xi, beta, order=1):
     return f
 
 
-def local_solve(st, v_it, it, cfg, grid, pinned=None):
+def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
     """Next iterate: G(v^p) for most particles; for the creeping ones a root of
     g(u) = G_i(u) - u with this iteration's fields fixed, per component.
 
@@ -257,20 +257,34 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
     * Otherwise: secant steps (factor clamped to [-OMEGA_MAX, OMEGA_MAX]) while each one at
       least halves |g|, so a nearby root is found first; else steps u + f g along g with
       f = 2, 4, 8, ... (g is continuous there and G bounded, so g changes sign that way);
-      inside a bracket, Illinois (modified regula falsi) steps.  At most LOCAL_STEPS
-      evaluations; each component's best iterate is kept.
+      inside a bracket, Illinois (modified regula falsi) steps.  A bracket whose interior
+      holds the velocity that lands the orbit exactly on a knot is first split there: the
+      orbit-averaged force changes steeply just past a knot (its weight is the fraction of
+      the path beyond it), so g is smooth only between such landing points, and regula falsi
+      across one can crawl along the flat side without reaching the root.  The components
+      share each evaluation, so a sign change of one component's g can come from another
+      component's move: a bracket whose same end is replaced three times running is released
+      and followed by a secant step.  At most LOCAL_STEPS evaluations, ending once one of
+      them has every component's |g| within LOCAL_TOL of the particle's speed; the
+      evaluation with the smallest largest-component |g| is kept (the components are
+      coupled, so a mix of components from different evaluations is no root).
 
     ``pinned`` (np, 3): components found sliding earlier in this step; they stay pinned, so
-    that the outer iteration cannot cycle between pinned and free.
-    Returns (v_next, slide mask)."""
+    that the outer iteration cannot cycle between pinned and free.  ``crept`` (np,): the
+    particles solved locally earlier in this step; they keep the local solve for the rest of
+    the step, so that no particle alternates between the local and the plain update.
+    Returns (v_next, slide mask, crept mask)."""
     H = np.asarray(grid.H)
     G = it["v_new"]
     v_next = G.copy()
     slide = np.zeros(G.shape, dtype=bool)
     beta = cfg.dt * 0.5 * (v_it + st.v) / H
-    idx = np.nonzero(creeping(st.xi, beta, cfg.order))[0]
+    local = creeping(st.xi, beta, cfg.order)
+    if crept is not None:
+        local = local | crept
+    idx = np.nonzero(local)[0]
     if idx.size == 0:
-        return v_next, slide
+        return v_next, slide, local
 
     def Gf(u):
         return push_particles(st.xi[idx], st.v[idx], st.P[idx], u, st.q, st.m, st.A, it["A"], it["gphi_half"],
@@ -300,14 +314,18 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
     r1 = Gf(u1) - u1
     r0 = np.where(sl, 0.0, r0)
     r1 = np.where(sl, 0.0, r1)
-    tol = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)[:, None]
-    best_u = np.where(sl | (np.abs(r1) < np.abs(r0)), u1, u0)
-    best_r = np.where(sl, 0.0, np.minimum(np.abs(r1), np.abs(r0)))
+    tol = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)
+    # the best evaluation so far: the smallest largest-component |g| (all components of one
+    # evaluation, since they are coupled; pinned components land on their knot)
+    m0, m1 = np.abs(r0).max(axis=1), np.abs(r1).max(axis=1)
+    best_u = np.where(sl, u_land, np.where((m1 < m0)[:, None], u1, u0))
+    best_r = np.minimum(m0, m1)
     br = ~sl & (r0 * r1 < 0)                          # bracketed components
     ua, ga, ub, gb = u0.copy(), r0.copy(), u1.copy(), r1.copy()
     side = np.zeros_like(u0)
     secant_ok = np.abs(r1) <= 0.5 * np.abs(r0)        # the plain step at least halved |g|
     fac = np.full_like(u0, 2.0)
+    rep = np.zeros(u0.shape, dtype=np.int64)          # consecutive replacements of one end
     for _ in range(LOCAL_STEPS - 1):
         if np.all(best_r <= tol):
             break
@@ -316,17 +334,27 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
             fp = ub - gb * (ub - ua) / (gb - ga)
         sec = np.where(np.isfinite(sec), np.clip(sec, -OMEGA_MAX, OMEGA_MAX), 1.0)
         expand = ~br & ~secant_ok
+        # the knot landing strictly inside the bracket (the highest one, if several)
+        lo, hi = np.minimum(ua, ub), np.maximum(ua, ub)
+        b_lo, b_hi = cfg.dt * 0.5 * (lo + vn) / H, cfg.dt * 0.5 * (hi + vn) / H
+        xk = x0 - koff
+        b_land = (np.ceil(xk + b_hi) - 1.0) - xk
+        u_split = 2.0 * b_land * H / cfg.dt - vn
+        split = br & (b_land > b_lo) & (u_split > lo) & (u_split < hi)
         u2 = np.where(br & np.isfinite(fp), fp, np.where(expand, u1 + fac * r1, u1 + sec * r1))
+        u2 = np.where(split, u_split, u2)
         u2 = np.where(sl, u_land, u2)
         fac = np.where(expand, 2.0 * fac, fac)
         r2 = np.where(sl, 0.0, Gf(u2) - u2)
-        better = ~sl & (np.abs(r2) < best_r)
-        best_u = np.where(better, u2, best_u)
-        best_r = np.where(better, np.abs(r2), best_r)
+        m2 = np.abs(r2).max(axis=1)
+        better = m2 < best_r
+        best_u = np.where(better[:, None], u2, best_u)
+        best_r = np.where(better, m2, best_r)
         secant_ok = secant_ok & (np.abs(r2) <= 0.5 * np.abs(r1))
         # bracket bookkeeping (Illinois: halve the kept end's value when it is kept twice)
         same_b = br & (r2 * gb > 0)
         same_a = br & ~same_b
+        side_before = side
         ga = np.where(same_b & (side > 0), 0.5 * ga, ga)
         gb = np.where(same_a & (side < 0), 0.5 * gb, gb)
         ub, gb = np.where(same_b, u2, ub), np.where(same_b, r2, gb)
@@ -336,12 +364,22 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None):
         ua, ga = np.where(new_br, u1, ua), np.where(new_br, r1, ga)
         ub, gb = np.where(new_br, u2, ub), np.where(new_br, r2, gb)
         br = br | new_br
+        # the same end replaced three times running: the kept end is stale (its g was taken
+        # before the other components moved: they share each evaluation) or regula falsi is
+        # crawling; the bracket is released and the next step is a secant one
+        rep = np.where((same_b & (side_before > 0)) | (same_a & (side_before < 0)), rep + 1,
+                       np.where(same_a | same_b, 1, rep))
+        release = br & (rep >= 3)
+        br = br & ~release
+        secant_ok = secant_ok | release
+        rep = np.where(release, 0, rep)
+        side = np.where(release, 0.0, side)
         u0, r0, u1, r1 = u1, r1, u2, r2
     v_next[idx] = best_u
     if pinned is not None:
         slide |= pinned
     slide[idx] = sl
-    return v_next, slide
+    return v_next, slide, local
 
 
 def j_scale(st, grid):
@@ -361,10 +399,11 @@ def step(st, cfg):
     hist = []
     converged = False
     slide = None
+    crept = None
     for p in range(cfg.picard_max + 1):
         it = picard_iteration(st, v_it, cfg, grid)
         if cfg.picard_accel:
-            v_next, slide = local_solve(st, v_it, it, cfg, grid, slide)
+            v_next, slide, crept = local_solve(st, v_it, it, cfg, grid, slide, crept)
         else:
             v_next, slide = it["v_new"], None
         vnorm = np.linalg.norm(v_next)

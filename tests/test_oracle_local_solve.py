@@ -1,0 +1,75 @@
+"""Pins of the oracle's particle-local solve (the accelerated fixed point that §4.8 allows).
+
+The local solve is only a means to a root: §4.8's conservation statements hold for the
+converged discrete equations, whatever solver reaches them.  So the pin is the defining
+property, not the path: with the iteration's fields fixed, every creeping particle that the
+solve does not pin onto a knot must satisfy its own push equation v = G_i(v) to roundoff.
+
+The state is built to make that hard: particles a hair (1e-6 .. 1e-3 cells) from a knot,
+drifting towards it by about that distance per step, with an extrapolated first iterate up
+to 0.05 cells away.  There the orbit-averaged force changes steeply just past the knot (its
+weight is the fraction of the path beyond it), which is where regula falsi crawls and where
+one component's large move can leave another component's bracket stale.
+"""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import pic
+
+
+def _knot_state(seed, far, npart=512):
+    n = (8, 8, 8)
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    cfg = pic.Config(n=n, L=w.L, dt=w.dt, picard_tol=1e-13)
+    H = np.asarray(cfg.grid().H)
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(0, 8, size=(npart, 3))
+    k = rng.integers(0, 8, size=npart).astype(float)
+    dk = 10.0 ** rng.uniform(-6, -3, size=npart)
+    s = rng.choice([-1.0, 1.0], size=npart)
+    xi[:, 1] = np.mod(k - s * dk, 8.0)                     # a hair short of a y knot
+    v = rng.normal(scale=0.05, size=(npart, 3))
+    v[:, 1] = s * dk * rng.uniform(0.0, 2.0, size=npart) * H[1] / cfg.dt   # drifting onto it
+    q = -1.0 / npart
+    st = pic.init(xi * H, v, q, abs(q), cfg)
+    vprev = st.v.copy()
+    vprev[:, 1] -= rng.uniform(-far, far, size=npart) * H[1] / cfg.dt      # a distant first iterate
+    return pic.replace(st, vprev=vprev), cfg
+
+
+@pytest.mark.parametrize("seed,far", [(5, 0.01), (5, 0.05), (6, 0.01), (6, 0.05)])
+def test_local_solve_reaches_a_root_for_every_creeping_particle(seed, far):
+    st, cfg = _knot_state(seed, far)
+    grid = cfg.grid()
+    H = np.asarray(grid.H)
+    v_it = 2.0 * st.v - st.vprev
+    it = pic.picard_iteration(st, v_it, cfg, grid)
+    v_next, slide, local = pic.local_solve(st, v_it, it, cfg, grid)
+    creeping = pic.creeping(st.xi, cfg.dt * 0.5 * (v_it + st.v) / H, cfg.order)
+    assert np.array_equal(local, creeping)
+    assert creeping.sum() > 200
+    G = pic.push_particles(st.xi, st.v, st.P, v_next, st.q, st.m, st.A, it["A"], it["gphi_half"],
+                           it["U_half"], cfg, grid)["v_new"]
+    resid = np.where(slide, 0.0, np.abs(G - v_next)).max(axis=1) / np.linalg.norm(v_next, axis=1)
+    assert resid[creeping].max() <= 4e-15
+    # the others took Algorithm 1's plain update
+    assert np.array_equal(v_next[~creeping], it["v_new"][~creeping])
+
+
+def test_crept_particles_keep_the_local_solve_for_the_step():
+    st, cfg = _knot_state(5, 0.01)
+    grid = cfg.grid()
+    v_it = 2.0 * st.v - st.vprev
+    it = pic.picard_iteration(st, v_it, cfg, grid)
+    _, _, local = pic.local_solve(st, v_it, it, cfg, grid)
+    # a particle solved locally once stays local, even where its iterate no longer creeps
+    crept = np.zeros_like(local)
+    crept[np.nonzero(~local)[0][:5]] = True
+    v_next, _, local2 = pic.local_solve(st, v_it, it, cfg, grid, None, crept)
+    assert np.array_equal(local2, local | crept)
+    G = pic.push_particles(st.xi, st.v, st.P, v_next, st.q, st.m, st.A, it["A"], it["gphi_half"],
+                           it["U_half"], cfg, grid)["v_new"]
+    resid = np.abs(G - v_next).max(axis=1) / np.linalg.norm(v_next, axis=1)
+    assert resid[crept].max() <= 4e-15
