@@ -28,13 +28,15 @@ Readings of points the paper leaves open (each is listed in the design notes):
   ``picard_accel`` each iteration therefore solves, for the creeping particles only, the
   particle's own equation v = G_i(v) with the iteration's fields held fixed (per component:
   secant steps while they converge, else growing steps along g until the root is bracketed,
-  then Illinois steps; at most LOCAL_STEPS evaluations; the best iterate is kept).  A
-  particle that barely crosses a knot can have no root near its iterate (the two sides of
-  the crossing threshold push the same way); g = G - u is continuous and G bounded, so a
-  root lies in the direction of g.  A particle that starts exactly on a knot can have no
-  root at all (G jumps where its orbit lands on the knot, both sides pushing onto it); it
-  then lands exactly on the knot and slides along it (Filippov solution; see local_solve),
-  which keeps the energy identities exact.  Every other
+  then bracketed steps that respect the knots; at most LOCAL_STEPS evaluations; the best
+  evaluation is kept; see local_solve).  A particle that barely crosses a knot can have no
+  root near its iterate (the two sides of the crossing threshold push the same way);
+  g = G - u is continuous and G bounded, so a root lies in the direction of g.  A particle
+  that starts on or a hair from a knot that both sides push it onto has no root that
+  double precision resolves (G changes by the full jump of d_a S within the hair); it then
+  lands exactly on the knot and slides along it (Filippov solution), which keeps the energy
+  identities to the size of its tiny vbar_a.  A particle solved locally once keeps the
+  local solve for the rest of the step.  Every other
   particle takes Algorithm 1's update v^{p+1} = G(v^p).  The outer loop then contracts at
   the rate of the weak particle-field coupling.  With ``picard_accel=False`` every particle
   takes the plain update.
@@ -54,7 +56,8 @@ from . import mesh, orbit
 CHUNK = 32768
 BETA_CREEP = 0.1      # cells: "creeping" knot crossings get a particle-local solve
 D_KNOT = 1e-6         # cells: starting this close to a knot also counts as creeping
-SLIDE_PROBE = 1e-12   # cells: the sliding test probes beta = d -+ SLIDE_PROBE
+SLIDE_PROBE = 1e-12   # cells: the sliding test probes SLIDE_PROBE short of landing on the knot
+SLIDE_FAR = 64.0      # ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it (98% of that path beyond)
 LOCAL_STEPS = 24      # at most this many extra push evaluations per creeping particle
 LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
 OMEGA_MAX = 8.0       # bound on the secant step factor
@@ -247,27 +250,33 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
     """Next iterate: G(v^p) for most particles; for the creeping ones a root of
     g(u) = G_i(u) - u with this iteration's fields fixed, per component.
 
-    * Sliding.  For a component starting within D_KNOT of a knot, g is probed just short of
-      and just past landing on that knot (beta_a = d -+ SLIDE_PROBE, d the signed distance).
-      If both sides push onto the knot there is no root: the orbit average of d_a S, and so
-      G, jumps there.  The component then lands exactly on the knot (beta_a = d, the
-      Filippov sliding solution) and the push completes it with v^{n+1}_a = u_a and P_a from
-      the canonical relation.  Energy is unaffected: the a-component work and the a-column
-      of D_i A are multiplied by vbar_a = d H_a / dt, which is below D_KNOT H_a / dt.
+    * Sliding.  For a component starting within D_KNOT of a knot (signed distance d), g is
+      probed SLIDE_PROBE short of landing on that knot and max(SLIDE_PROBE, SLIDE_FAR |d|)
+      past it, where the path beyond the knot carries most of the orbit average.  If both
+      sides push onto the knot, the root lies within that hair of the knot, where G changes
+      by the full jump of the orbit-averaged d_a S: double precision does not resolve it.
+      The component then lands exactly on the knot (beta_a = d, the Filippov sliding
+      solution) and the push completes it with v^{n+1}_a = u_a and P_a from the canonical
+      relation.  The energy identities are kept to the size of the a-component work and
+      a-column of D_i A, both multiplied by vbar_a = d H_a / dt < D_KNOT H_a / dt.
     * Otherwise: secant steps (factor clamped to [-OMEGA_MAX, OMEGA_MAX]) while each one at
       least halves |g|, so a nearby root is found first; else steps u + f g along g with
       f = 2, 4, 8, ... (g is continuous there and G bounded, so g changes sign that way);
-      inside a bracket, Illinois (modified regula falsi) steps.  A bracket whose interior
-      holds the velocity that lands the orbit exactly on a knot is first split there: the
-      orbit-averaged force changes steeply just past a knot (its weight is the fraction of
-      the path beyond it), so g is smooth only between such landing points, and regula falsi
-      across one can crawl along the flat side without reaching the root.  The components
-      share each evaluation, so a sign change of one component's g can come from another
-      component's move: a bracket whose same end is replaced three times running is released
-      and followed by a secant step.  At most LOCAL_STEPS evaluations, ending once one of
-      them has every component's |g| within LOCAL_TOL of the particle's speed; the
-      evaluation with the smallest largest-component |g| is kept (the components are
-      coupled, so a mix of components from different evaluations is no root).
+      inside a bracket, the new point replaces the end of the same sign:
+      - a bracket whose interior holds the velocity that lands the orbit exactly on a knot
+        is first split there: the force weight of the path beyond a knot makes G steep just
+        past it, so g is smooth only between such landings;
+      - inside one knot-free piece past a crossing (landing beta_L), G in cells is close to
+        A + B beta_L / beta: steep near the knot, flat far past it.  The step solves
+        beta = A + B beta_L / beta exactly for the line through the two ends (a quadratic
+        in beta, its root inside the bracket); elsewhere it is the regula falsi point;
+      - the components share each evaluation, so one component's sign change can come from
+        another component's move, and regula falsi can stagnate: a bracket whose same end
+        is replaced twice running is released and followed by a secant step.
+      At most LOCAL_STEPS evaluations, ending once one of them has every component's |g|
+      within LOCAL_TOL of the particle's speed; the evaluation with the smallest
+      largest-component |g| is kept (the components are coupled, so a mix of components
+      from different evaluations is no root).
 
     ``pinned`` (np, 3): components found sliding earlier in this step; they stay pinned, so
     that the outer iteration cannot cycle between pinned and free.  ``crept`` (np,): the
@@ -304,9 +313,11 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         cand = near[:, a] & ~sl[:, a]
         if not np.any(cand):
             continue
+        d = d_knot[:, a]
+        far = np.maximum(SLIDE_PROBE, SLIDE_FAR * np.abs(d))
         um, up = u1.copy(), u1.copy()
-        um[:, a] = 2.0 * (d_knot[:, a] - SLIDE_PROBE) * H[a] / cfg.dt - vn[:, a]
-        up[:, a] = 2.0 * (d_knot[:, a] + SLIDE_PROBE) * H[a] / cfg.dt - vn[:, a]
+        um[:, a] = 2.0 * (d - np.where(d > 0, SLIDE_PROBE, far)) * H[a] / cfg.dt - vn[:, a]
+        up[:, a] = 2.0 * (d + np.where(d > 0, far, SLIDE_PROBE)) * H[a] / cfg.dt - vn[:, a]
         gm = Gf(um)[:, a] - um[:, a]
         gp = Gf(up)[:, a] - up[:, a]
         sl[:, a] |= cand & (gm > 0) & (gp < 0)
@@ -326,18 +337,41 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
     secant_ok = np.abs(r1) <= 0.5 * np.abs(r0)        # the plain step at least halved |g|
     fac = np.full_like(u0, 2.0)
     rep = np.zeros(u0.shape, dtype=np.int64)          # consecutive replacements of one end
+    c = cfg.dt * 0.5 / H                              # beta = c (u + v^n): orbit length in cells
+    xk = x0 - koff                                    # start on the knot lattice
     for _ in range(LOCAL_STEPS - 1):
         if np.all(best_r <= tol):
             break
         with np.errstate(divide="ignore", invalid="ignore"):
             sec = -(u1 - u0) / (r1 - r0)
             fp = ub - gb * (ub - ua) / (gb - ga)
+            # Both ends past the same last knot (landing beta_L): on that knot-free piece the
+            # image G, in cells, is close to A + B w with w = beta_L / beta (the path beyond
+            # the knot weights the force there), steep near the knot and flat far past it.
+            # The step solves beta = A + B w exactly for the line through the two ends:
+            # D beta^2 - c1 beta - e = 0, its root inside the bracket.
+            ba, bb = c * (ua + vn), c * (ub + vn)
+            la = np.where(ba > 0, np.floor(xk + ba) - xk, np.ceil(xk + ba) - xk)
+            lb = np.where(bb > 0, np.floor(xk + bb) - xk, np.ceil(xk + bb) - xk)
+            Ga, Gb = c * ga + ba, c * gb + bb
+            wa, wb = la / ba, la / bb
+            D = wb - wa
+            c1 = Ga * D - (Gb - Ga) * wa
+            e = (Gb - Ga) * la
+            qq = 0.5 * (c1 + np.copysign(np.sqrt(np.maximum(c1 * c1 + 4.0 * D * e, 0.0)), c1))
+            x1, x2 = qq / D, -e / qq
+            blo, bhi = np.minimum(ba, bb), np.maximum(ba, bb)
+            in1, in2 = (x1 > blo) & (x1 < bhi), (x2 > blo) & (x2 < bhi)
+            bstar = np.where(in1, x1, x2)
+            fpm = 2.0 * bstar * H / cfg.dt - vn
+            piece = ((la == lb) & (la != 0.0) & (la * ba > 0) & (la * bb > 0) & (c1 * c1 + 4.0 * D * e >= 0.0)
+                     & (in1 | in2) & np.isfinite(fpm))
+        fp = np.where(piece, fpm, fp)
         sec = np.where(np.isfinite(sec), np.clip(sec, -OMEGA_MAX, OMEGA_MAX), 1.0)
         expand = ~br & ~secant_ok
         # the knot landing strictly inside the bracket (the highest one, if several)
         lo, hi = np.minimum(ua, ub), np.maximum(ua, ub)
-        b_lo, b_hi = cfg.dt * 0.5 * (lo + vn) / H, cfg.dt * 0.5 * (hi + vn) / H
-        xk = x0 - koff
+        b_lo, b_hi = c * (lo + vn), c * (hi + vn)
         b_land = (np.ceil(xk + b_hi) - 1.0) - xk
         u_split = 2.0 * b_land * H / cfg.dt - vn
         split = br & (b_land > b_lo) & (u_split > lo) & (u_split < hi)
@@ -351,12 +385,10 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         best_u = np.where(better[:, None], u2, best_u)
         best_r = np.where(better, m2, best_r)
         secant_ok = secant_ok & (np.abs(r2) <= 0.5 * np.abs(r1))
-        # bracket bookkeeping (Illinois: halve the kept end's value when it is kept twice)
+        # bracket bookkeeping: the new point replaces the end whose g has its sign
         same_b = br & (r2 * gb > 0)
         same_a = br & ~same_b
         side_before = side
-        ga = np.where(same_b & (side > 0), 0.5 * ga, ga)
-        gb = np.where(same_a & (side < 0), 0.5 * gb, gb)
         ub, gb = np.where(same_b, u2, ub), np.where(same_b, r2, gb)
         ua, ga = np.where(same_a, u2, ua), np.where(same_a, r2, ga)
         side = np.where(same_b, 1.0, np.where(same_a, -1.0, side))
@@ -364,12 +396,12 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         ua, ga = np.where(new_br, u1, ua), np.where(new_br, r1, ga)
         ub, gb = np.where(new_br, u2, ub), np.where(new_br, r2, gb)
         br = br | new_br
-        # the same end replaced three times running: the kept end is stale (its g was taken
-        # before the other components moved: they share each evaluation) or regula falsi is
-        # crawling; the bracket is released and the next step is a secant one
+        # the same end replaced twice running: the kept end is stale (its g was taken before
+        # the other components moved: they share each evaluation) or regula falsi stagnates;
+        # the bracket is released and the next step is a secant one from two fresh points
         rep = np.where((same_b & (side_before > 0)) | (same_a & (side_before < 0)), rep + 1,
                        np.where(same_a | same_b, 1, rep))
-        release = br & (rep >= 3)
+        release = br & (rep >= 2)
         br = br & ~release
         secant_ok = secant_ok | release
         rep = np.where(release, 0, rep)
