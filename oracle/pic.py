@@ -55,7 +55,9 @@ from . import mesh, orbit
 
 CHUNK = 32768
 BETA_CREEP = 0.1      # cells: "creeping" knot crossings get a particle-local solve
-D_KNOT = 1e-6         # cells: starting this close to a knot also counts as creeping
+D_KNOT = 1e-11        # cells: starting this close to a knot counts as creeping and is probed
+                      # for sliding (about the rounding of a position landed on a knot, with
+                      # margin: farther out the knot-piece step resolves the root)
 SLIDE_PROBE = 1e-12   # cells: the sliding test probes SLIDE_PROBE short of landing on the knot
 SLIDE_FAR = 64.0      # ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it (98% of that path beyond)
 LOCAL_STEPS = 24      # at most this many extra push evaluations per creeping particle
