@@ -335,6 +335,13 @@ def main():
                              "at 2010 MHz)",
                 "share_of_step": (prof.push_ms / ms) if ms > 0 else None,
                 "mean_orbit_pieces": mean_pieces}
+    # the particle-local solves of the creeping particles (their own kernel, after each push)
+    local = None
+    if prof.local_launches:
+        local = {"kernel": "k_local", "share_of_step": prof.local_ms / ms if ms > 0 else None,
+                 "ms_per_launch": prof.local_ms / prof.local_launches,
+                 "solves_per_launch": prof.local_solves / prof.local_launches,
+                 "evals_per_solve": prof.local_evals / prof.local_solves if prof.local_solves else None}
 
     # end to end through the public API: the full state crosses host <-> device every step
     e2e = None
@@ -419,6 +426,7 @@ def main():
                        "mean_fp32_iterations": info.total_iterations_fp32 / max(info.steps_done, 1),
                        "relative_energy_drift": drift},
             "roofline": roofline,
+            "local_solves": local,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(prof.launches),

@@ -197,6 +197,10 @@ typedef struct {
     int64_t scatter_pieces;      /* orbit pieces integrated by their next-orbit scatters */
     int64_t push32_launches;     /* FP32 push + scatter launches (PIC_MIXED) */
     double push32_ms;
+    int64_t local_launches;      /* particle-local solve launches (picard_accel = 1), one per FP64 push */
+    double local_ms;             /* their summed event durations (not part of push_ms) */
+    int64_t local_solves;        /* creeping particles solved by them */
+    int64_t local_evals;         /* push evaluations those solves made (probes, first, iterations) */
 } pic_profile_t;
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,

@@ -149,6 +149,10 @@ class PicProfile(C.Structure):
         ("scatter_pieces", C.c_int64),
         ("push32_launches", C.c_int64),
         ("push32_ms", C.c_double),
+        ("local_launches", C.c_int64),
+        ("local_ms", C.c_double),
+        ("local_solves", C.c_int64),
+        ("local_evals", C.c_int64),
     ]
 
 

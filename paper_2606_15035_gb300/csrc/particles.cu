@@ -599,7 +599,9 @@ __global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, con
 constexpr int LOCAL_STEPS = 24;      // push evaluations per creeping particle
 constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
 constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
-constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes beta = d -+ SLIDE_PROBE
+constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes SLIDE_PROBE short of the knot
+constexpr double SLIDE_FAR = 64.0;    // ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it
+constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
 
 struct PushOut {
     double Pw[3], xe[3], Ae[3], vw[3];
@@ -711,7 +713,9 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
                     wv[a] = p.q_dV * vb2;
                 }
                 const double xk[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};   // knot lattice
-                const bool creep = p.accel && is_creeping(xk, beta_it);
+                // a particle solved locally earlier in this step keeps the local solve, so that
+                // none alternates between it and the plain update
+                const bool creep = p.accel && (is_creeping(xk, beta_it) || (slide[i] & SLIDE_CREPT));
                 if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
                 if (creep) {
                     if (!creep_flag) {
@@ -778,17 +782,29 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
 // g(u) = G_i(u) - u, starting from (v^p, G(v^p)): clamped secant steps while each one at
 // least halves |g| (a nearby root is found first); otherwise steps u + f g with f = 2, 4,
 // 8, ... (g is continuous and G bounded, so g changes sign that way: a particle that barely
-// crosses a knot can have no root near its iterate); inside a bracket, Illinois (modified
-// regula falsi) steps.  At most LOCAL_STEPS push evaluations, stopping when every
-// component's residual is below LOCAL_TOL times the particle's speed; each component's best
-// iterate is kept.  Sliding (sticky for the rest of the step once detected, so that the
-// outer iteration cannot cycle between pinned and free): a component starting within D_KNOT
-// of a knot whose two sides
-// (beta_a = d -+ SLIDE_PROBE, d the signed distance) both push onto the knot has no root (G
-// jumps there); it lands exactly on the knot (the Filippov solution) and the commit push sets
-// v^{n+1}_a to it with P_a from the canonical relation; vbar_a = d H / dt < D_KNOT H / dt, so
-// the energy identities are unaffected.  The plain image G(v^p) is saved in gsave
-// (diagnostics), then the orbit current of the result is scattered.
+// crosses a knot can have no root near its iterate).  Inside a bracket the new point replaces
+// the end of its sign:
+//  - a bracket holding the velocity that lands the orbit exactly on a knot is first split
+//    there: the force weight of the path beyond a knot makes G steep just past it, so g is
+//    smooth only between landings;
+//  - inside one knot-free piece past a crossing (landing beta_L), G in cells is close to
+//    A + B beta_L / beta; the step solves beta = A + B beta_L / beta exactly for the line
+//    through the two ends (a quadratic), elsewhere it is the regula falsi point;
+//  - the components share each evaluation, so another component's move can leave a bracket
+//    stale, and regula falsi can stagnate: a bracket whose same end is replaced twice running
+//    is released for a secant step.
+// At most LOCAL_STEPS push evaluations, stopping once one evaluation has every component's
+// residual below LOCAL_TOL times the particle's speed; the evaluation with the smallest
+// largest-component residual is kept whole (the components are coupled).  A particle solved
+// here keeps the local solve for the rest of the step (SLIDE_CREPT), so that none alternates
+// between it and the plain update.  Sliding (sticky for the rest of the step once detected,
+// so that the outer iteration cannot cycle between pinned and free): a component starting
+// within D_KNOT of a knot (signed distance d) whose two sides, probed SLIDE_PROBE short of
+// the landing and max(SLIDE_PROBE, SLIDE_FAR |d|) past it, both push onto the knot has no
+// root that double precision resolves; it lands exactly on the knot (the Filippov solution)
+// and the commit push sets v^{n+1}_a to it with P_a from the canonical relation.  The energy
+// identities hold to the size of vbar_a = d H / dt < D_KNOT H / dt.  The plain image G(v^p)
+// is saved in gsave (diagnostics), then the orbit current of the result is scattered.
 template <int QUAD>
 __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* __restrict__ xi,
                                                    const double* __restrict__ v, const double* __restrict__ P,
@@ -817,10 +833,12 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
     bool active = false, exhausted = false;
     int64_t i = 0;
     int phase = 0, paxis = 0, nstep = 0;
-    double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3], br[3];
+    double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3];
     double ua[3], ga[3], ub[3], gb[3], side[3], fac[3], uland[3], dk[3], ue[3];
     bool brk[3], secok[3], sl[3], probe[3];
-    double tol = 0.0, gm = 0.0;
+    int nrep[3];
+    double tol = 0.0, gm = 0.0, brs = 0.0;
+    double nsolve = 0.0, neval = 0.0;
     while (true) {
         if (!active && !exhausted) {
             int64_t k = -1;
@@ -871,28 +889,65 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
         // the evaluation point of this round
         if (active) {
             if (phase <= 1) {
-                // Sliding probes: a component starting within D_KNOT of a knot is tested just
-                // short of and just past landing on it (beta_a = d -+ SLIDE_PROBE); if both sides
-                // push onto the knot there is no root (G jumps there) and it lands on the knot.
+                // Sliding probes: a component starting within D_KNOT of a knot (signed distance
+                // d) is tested SLIDE_PROBE short of landing on it and max(SLIDE_PROBE,
+                // SLIDE_FAR |d|) past it, where the path beyond the knot carries most of the
+                // orbit average; if both sides push onto the knot, the root lies within that
+                // hair, unresolved in double precision, and the component lands on the knot.
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ue[a] = u1[a];
-                const double sg = phase == 0 ? -SLIDE_PROBE : SLIDE_PROBE;
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    if (a == paxis) ue[a] = 2.0 * (dk[a] + sg) * p.H[a] / p.dt - vn[a];
+                    if (a == paxis) {
+                        const double d = dk[a], far = fmax(SLIDE_PROBE, SLIDE_FAR * fabs(d));
+                        ue[a] = phase == 0 ? 2.0 * (d - (d > 0.0 ? SLIDE_PROBE : far)) * p.H[a] / p.dt - vn[a]
+                                           : 2.0 * (d + (d > 0.0 ? far : SLIDE_PROBE)) * p.H[a] / p.dt - vn[a];
+                    }
             } else if (phase == 2) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ue[a] = u1[a];
             } else {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const double fp = ub[a] - gb[a] * (ub[a] - ua[a]) / (gb[a] - ga[a]);
+                    const double c = p.dt * 0.5 / p.H[a];   // beta = c (u + v^n), in cells
+                    const double xk = x0[a] - p.koff;        // start on the knot lattice
+                    double fp = ub[a] - gb[a] * (ub[a] - ua[a]) / (gb[a] - ga[a]);
+                    {
+                        // Both ends past the same last knot (landing beta_L): on that knot-free
+                        // piece the image G in cells is close to A + B w, w = beta_L / beta, steep
+                        // near the knot and flat far past it; solve beta = A + B w exactly for the
+                        // line through the two ends (D beta^2 - c1 beta - e = 0, root in bracket).
+                        const double ba = c * (ua[a] + vn[a]), bb = c * (ub[a] + vn[a]);
+                        const double la = ba > 0.0 ? floor(xk + ba) - xk : ceil(xk + ba) - xk;
+                        const double lb = bb > 0.0 ? floor(xk + bb) - xk : ceil(xk + bb) - xk;
+                        const double Ga = c * ga[a] + ba, Gb = c * gb[a] + bb;
+                        const double wa = la / ba, wb = la / bb;
+                        const double D = wb - wa;
+                        const double c1 = Ga * D - (Gb - Ga) * wa;
+                        const double e = (Gb - Ga) * la;
+                        const double disc = c1 * c1 + 4.0 * D * e;
+                        const double qq = 0.5 * (c1 + copysign(sqrt(fmax(disc, 0.0)), c1));
+                        const double x1 = qq / D, x2 = -e / qq;
+                        const double bl = fmin(ba, bb), bh = fmax(ba, bb);
+                        const bool in1 = x1 > bl && x1 < bh, in2 = x2 > bl && x2 < bh;
+                        const double fpm = 2.0 * (in1 ? x1 : x2) * p.H[a] / p.dt - vn[a];
+                        if (la == lb && la != 0.0 && la * ba > 0.0 && la * bb > 0.0 && disc >= 0.0 && (in1 || in2) &&
+                            isfinite(fpm))
+                            fp = fpm;
+                    }
                     double sec = -(u1[a] - u0[a]) / (r1[a] - r0[a]);
                     sec = isfinite(sec) ? fmin(fmax(sec, -OMEGA_MAX), OMEGA_MAX) : 1.0;
+                    // the knot landing strictly inside the bracket (the highest one, if several)
+                    const double lo = fmin(ua[a], ub[a]), hi = fmax(ua[a], ub[a]);
+                    const double blo = c * (lo + vn[a]), bhi = c * (hi + vn[a]);
+                    const double bland = (ceil(xk + bhi) - 1.0) - xk;
+                    const double usplit = 2.0 * bland * p.H[a] / p.dt - vn[a];
                     if (sl[a]) {
                         ue[a] = uland[a];                    // pinned: lands on the knot
+                    } else if (brk[a] && bland > blo && usplit > lo && usplit < hi) {
+                        ue[a] = usplit;                      // split the bracket where G kinks
                     } else if (brk[a] && isfinite(fp)) {
-                        ue[a] = fp;                          // Illinois inside the bracket
+                        ue[a] = fp;                          // bracketed step
                     } else if (!brk[a] && !secok[a]) {
                         ue[a] = u1[a] + fac[a] * r1[a];      // grow along g until g changes sign
                         fac[a] *= 2.0;
@@ -907,6 +962,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
         if (active) {
             push_eval<QUAD, false>(p, x0, vn, Pn, ue, table, acc, o);
             if (phase >= 2 && o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+            neval += 1.0;
         }
         if (!active) continue;
         bool done = false;
@@ -927,13 +983,13 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                 phase = 2;
             }
         } else if (phase == 2) {
+            double m0 = 0.0, m1 = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 r1[a] = sl[a] ? 0.0 : o.vw[a] - u1[a];
                 if (sl[a]) r0[a] = 0.0;
-                const bool b1 = sl[a] || fabs(r1[a]) < fabs(r0[a]);
-                bu[a] = b1 ? u1[a] : u0[a];
-                br[a] = sl[a] ? 0.0 : (b1 ? fabs(r1[a]) : fabs(r0[a]));
+                m0 = fmax(m0, fabs(r0[a]));
+                m1 = fmax(m1, fabs(r1[a]));
                 brk[a] = !sl[a] && r0[a] * r1[a] < 0.0;
                 ua[a] = u0[a];
                 ga[a] = r0[a];
@@ -942,29 +998,52 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                 side[a] = 0.0;
                 secok[a] = fabs(r1[a]) <= 0.5 * fabs(r0[a]);
                 fac[a] = 2.0;
+                nrep[a] = 0;
             }
+            // the best evaluation so far, whole (the components are coupled): the smallest
+            // largest-component |g|; pinned components land on their knot
+            const bool take1 = m1 < m0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bu[a] = sl[a] ? uland[a] : (take1 ? u1[a] : u0[a]);
+            brs = fmin(m0, m1);
             phase = 3;
-            done = nstep >= LOCAL_STEPS - 1 || (br[0] <= tol && br[1] <= tol && br[2] <= tol);
+            done = nstep >= LOCAL_STEPS - 1 || brs <= tol;
         } else {
+            double r2v[3], m2 = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const double r2 = sl[a] ? 0.0 : o.vw[a] - ue[a];
-                if (!sl[a] && fabs(r2) < br[a]) {
-                    br[a] = fabs(r2);
-                    bu[a] = ue[a];
-                }
+                r2v[a] = sl[a] ? 0.0 : o.vw[a] - ue[a];
+                m2 = fmax(m2, fabs(r2v[a]));
+            }
+            if (m2 < brs) {
+                brs = m2;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) bu[a] = ue[a];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double r2 = r2v[a];
                 secok[a] = secok[a] && fabs(r2) <= 0.5 * fabs(r1[a]);
                 if (brk[a]) {
                     if (r2 * gb[a] > 0.0) {            // replaces the b end
-                        if (side[a] > 0.0) ga[a] *= 0.5;
+                        nrep[a] = side[a] > 0.0 ? nrep[a] + 1 : 1;
                         ub[a] = ue[a];
                         gb[a] = r2;
                         side[a] = 1.0;
                     } else {                           // replaces the a end
-                        if (side[a] < 0.0) gb[a] *= 0.5;
+                        nrep[a] = side[a] < 0.0 ? nrep[a] + 1 : 1;
                         ua[a] = ue[a];
                         ga[a] = r2;
                         side[a] = -1.0;
+                    }
+                    // the same end replaced twice running: the kept end is stale (its g was
+                    // taken before the other components moved) or regula falsi stagnates;
+                    // released, the next step is a secant one from two fresh points
+                    if (nrep[a] >= 2) {
+                        brk[a] = false;
+                        secok[a] = true;
+                        nrep[a] = 0;
+                        side[a] = 0.0;
                     }
                 } else if (!sl[a] && r2 * r1[a] < 0.0) {
                     brk[a] = true;
@@ -979,7 +1058,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                 r1[a] = r2;
             }
             ++nstep;
-            done = nstep >= LOCAL_STEPS - 1 || (br[0] <= tol && br[1] <= tol && br[2] <= tol);
+            done = nstep >= LOCAL_STEPS - 1 || brs <= tol;
         }
         if (!done) continue;
         // the particle's solve is over: its best iterate, sliding marks, e_v terms and current
@@ -990,7 +1069,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                 bu[a] = uland[a];
                 sb |= (uint8_t)(1u << a);
             }
-        slide[i] = sb;
+        slide[i] = sb | SLIDE_CREPT;
         double wv[3], bet2[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -1004,10 +1083,13 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
             wv[a] = p.q_dV * vb2;
         }
         if (scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext) < 0) atomicOr(status, DEV_ERR_SEGMENTS);
+        nsolve += 1.0;
         active = false;
     }
     write_partial<double>(partials, S_EVL_NUM, ev_num, sm, false);
     write_partial<double>(partials, S_EVL_DEN, ev_den, sm, false);
+    write_partial<double>(partials, S_LOCAL_SOLVES, nsolve, sm, false);
+    write_partial<double>(partials, S_LOCAL_EVALS, neval, sm, false);
 }
 
 __global__ void k_kinetic(StepParams p, const double* __restrict__ v, double* __restrict__ partials) {
@@ -1288,7 +1370,7 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
 #define PIC_PUSH(Q, C, D)                                                                                        \
     k_push<Q, C, D><<<nb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, Jnext, c.xi_new, c.P_new, \
                                                   c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,  \
-                                                  commit ? c.slide : nullptr,                                 \
+                                                  c.slide,                                                    \
                                                   c.partials, c.dev_status)
     if (!commit) {
         if (closed) PIC_PUSH(0, false, false);
@@ -1302,18 +1384,23 @@ void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool co
     }
 #undef PIC_PUSH
     ++c.launches;
-    if (!commit && c.cfg.picard_accel) {
-        int lb = local_blocks(c);
-        if (closed)
-            k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
-                                                     c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
-                                                     c.slide, c.creep_count + 1, c.partials, c.dev_status);
-        else
-            k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext,
-                                                     c.creep_list, c.creep_count, det ? c.creep_flag : nullptr,
-                                                     c.slide, c.creep_count + 1, c.partials, c.dev_status);
-        ++c.launches;
-    }
+    // in deterministic mode the exact current is rounded once all of its deposits are in
+    if (det && Jnext && !c.cfg.picard_accel) launch_exact_finish(c, Jnext, 3 * c.m.ncell, c.inv_u_J);
+}
+
+void launch_local(Ctx& c, const double* vit, double* vnew, double* Jnext) {
+    StepParams p = make_params(c);
+    const bool det = c.cfg.deterministic != 0;
+    const int lb = local_blocks(c);
+    if (c.cfg.quadrature == PIC_QUAD_CLOSED)
+        k_local<0><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext, c.creep_list,
+                                                 c.creep_count, det ? c.creep_flag : nullptr, c.slide,
+                                                 c.creep_count + 1, c.partials, c.dev_status);
+    else
+        k_local<1><<<lb, THREADS, 0, c.stream>>>(p, c.xi, c.v, c.P, vit, c.table, vnew, c.gsave, Jnext, c.creep_list,
+                                                 c.creep_count, det ? c.creep_flag : nullptr, c.slide,
+                                                 c.creep_count + 1, c.partials, c.dev_status);
+    ++c.launches;
     if (det && Jnext) launch_exact_finish(c, Jnext, 3 * c.m.ncell, c.inv_u_J);
 }
 

@@ -147,6 +147,7 @@ void prof_resolve(Ctx& c) {
             case PH_MESH: c.prof_acc.mesh_ms += ms; break;
             case PH_SORT: c.prof_acc.sort_ms += ms; break;
             case PH_PUSH32: c.prof_acc.push32_ms += ms; c.prof_acc.push32_launches += 1; break;
+            case PH_LOCAL: c.prof_acc.local_ms += ms; c.prof_acc.local_launches += 1; break;
             default: break;
         }
         c.ev_pool.push_back(pe.second.first);
@@ -485,10 +486,15 @@ void iter_issue(Ctx& c) {
             ProfScope ps(c, PH_PUSH);
             launch_push(c, c.vit, c.vnew, c.J[r.next], false, false);
         }
+        if (c.cfg.picard_accel) {
+            ProfScope ps(c, PH_LOCAL);
+            launch_local(c, c.vit, c.vnew, c.J[r.next]);
+        }
         launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
         if (c.cfg.picard_accel) launch_finalize(c, S_EVL_NUM, 2, local_blocks(c), false);
         launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
         if (c.prof) launch_finalize(c, S_PIECES_PUSH, 2, particle_blocks(c), false);
+        if (c.prof && c.cfg.picard_accel) launch_finalize(c, S_LOCAL_SOLVES, 2, local_blocks(c), false);
         c.last_v = c.vit;
         c.last_g = c.vnew;
     }
@@ -536,6 +542,10 @@ pic_status iter_finish(pic_ctx* ctx) {
         if (c.prof) {
             c.prof_acc.push_pieces += (int64_t)h[S_PIECES_PUSH];
             c.prof_acc.scatter_pieces += (int64_t)h[S_PIECES_SCATTER];
+            if (c.cfg.picard_accel) {
+                c.prof_acc.local_solves += (int64_t)h[S_LOCAL_SOLVES];
+                c.prof_acc.local_evals += (int64_t)h[S_LOCAL_EVALS];
+            }
         }
         double num = h[S_EV_NUM], den = h[S_EV_DEN];
         if (c.cfg.picard_accel) {
@@ -1043,7 +1053,10 @@ pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push
         int best_bps = c.push_bps;
         for (int bps : cand) {
             c.push_bps = bps;
-            const float ms = time_launches(c, 2, [&] { launch_push(c, c.vit, c.vnew, c.J[1], false, false); });
+            const float ms = time_launches(c, 2, [&] {
+                launch_push(c, c.vit, c.vnew, c.J[1], false, false);
+                if (c.cfg.picard_accel) launch_local(c, c.vit, c.vnew, c.J[1]);
+            });
             if (ms < best) {
                 best = ms;
                 best_bps = bps;

@@ -320,7 +320,9 @@ __device__ __forceinline__ void exact_add(const ExactAcc& a, int64_t idx, double
 // ---- "creeping" orbits --------------------------------------------------------------------
 
 constexpr double BETA_CREEP = 0.1;   // cells
-constexpr double D_KNOT = 1e-6;      // cells: starting this close to a knot also counts
+constexpr double D_KNOT = 1e-11;     // cells: starting this close to a knot also counts (and is
+                                     // probed for sliding: about the rounding of a position
+                                     // landed on a knot, with margin)
 
 // On an axis where the orbit moves less than BETA_CREEP cells, does it get within 2 |beta|
 // of the next knot ahead, or start within D_KNOT of any knot?  Those orbits cross a knot

@@ -40,6 +40,8 @@ enum Slot : int {
     S_K,           // kinetic energy of the current state
     S_PIECES_PUSH,     // orbit pieces visited by the push (profiling)
     S_PIECES_SCATTER,  // orbit pieces visited by the scatter of the next orbit (profiling)
+    S_LOCAL_SOLVES,    // particle-local solves made by k_local (profiling)
+    S_LOCAL_EVALS,     // push evaluations made by those solves (profiling)
     S_PROJ0,       // 8 null-mode projections (init)
     S_NULLSTAT = S_PROJ0 + 8,
     NSLOT
@@ -171,7 +173,7 @@ struct Ctx {
     double K_n = 0, W_n = 0;
 };
 
-enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_PUSH32 };
+enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_PUSH32, PH_LOCAL };
 
 // ---- launchers (particles.cu) ----
 void launch_init_positions(Ctx& c, const double* x_dev);
@@ -179,6 +181,8 @@ void launch_point_deposit(Ctx& c);
 void launch_sort(Ctx& c);
 void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null);
 void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag);
+// The particle-local solves of the creeping particles that the last (non-commit) push listed.
+void launch_local(Ctx& c, const double* vit, double* vnew, double* Jnext);
 void launch_kinetic(Ctx& c);
 void launch_unpermute(Ctx& c, const double* src_soa3, double* dst_soa3, double scale0, double scale1, double scale2);
 void launch_patch_local(Ctx& c, double* g);
