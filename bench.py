@@ -145,7 +145,7 @@ def time_oracle(w, npart, steps, warmup):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import pic as opic
     x, v, q, m = oracle_sample(w, npart)
-    cfg = opic.Config(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol)
+    cfg = opic.Config(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max)
     st = opic.init(x, v, q, m, cfg)
     for _ in range(warmup):
         st, info = opic.step(st, cfg)
@@ -197,7 +197,8 @@ def run_ensemble(args, world, rank, local):
     items = []
     for r in runs:
         x, v, q, m = pi.ensemble_particles(r)
-        items.append((sim.pic_config_default(n=r.n, L=r.L, dt=r.dt, picard_tol=r.picard_tol, precision=prec),
+        items.append((sim.pic_config_default(n=r.n, L=r.L, dt=r.dt, picard_tol=r.picard_tol, picard_max=r.picard_max,
+                                             precision=prec),
                       x, v, q, m))
     total = sum(r.n_particles for r in runs)
     ens = sim.PicEnsemble(items, autotune=True)
@@ -283,7 +284,7 @@ def main():
         extra = {"ops": 1 if args.ops == "spectral" else 0, "deterministic": int(args.deterministic)}
         if args.shape_order > 1:
             extra.update(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
-        cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol,
+        cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max,
                                      precision=1 if precision == "mixed" else 0, **extra)
         sm = sim.PicSim(cfg, x, v, q, m)
         e_start = sm.energy().total

@@ -35,8 +35,9 @@ Readings of points the paper leaves open (each is listed in the design notes):
   that starts on or a hair from a knot that both sides push it onto has no root that
   double precision resolves (G changes by the full jump of d_a S within the hair); it then
   lands exactly on the knot and slides along it (Filippov solution), which keeps the energy
-  identities to the size of its tiny vbar_a.  A particle solved locally once keeps the
-  local solve for the rest of the step.  Every other
+  identities to the size of its tiny vbar_a.  So does a particle whose iterate change has
+  stopped shrinking faster than SLOW_RATIO per iteration (see slow_particles).  A particle
+  solved locally once keeps the local solve for the rest of the step.  Every other
   particle takes Algorithm 1's update v^{p+1} = G(v^p).  The outer loop then contracts at
   the rate of the weak particle-field coupling.  With ``picard_accel=False`` every particle
   takes the plain update.
@@ -60,9 +61,11 @@ D_KNOT = 1e-11        # cells: starting this close to a knot counts as creeping 
                       # margin: farther out the knot-piece step resolves the root)
 SLIDE_PROBE = 1e-12   # cells: the sliding test probes SLIDE_PROBE short of landing on the knot
 SLIDE_FAR = 64.0      # ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it (98% of that path beyond)
-LOCAL_STEPS = 24      # at most this many extra push evaluations per creeping particle
+LOCAL_STEPS = 32      # at most this many extra push evaluations per creeping particle
 LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
 OMEGA_MAX = 8.0       # bound on the secant step factor
+SLOW_RATIO = 0.25     # a plain particle whose change did not shrink below SLOW_RATIO of the
+SLOW_FLOOR = 1e-12   # previous one (and exceeds SLOW_FLOOR x its speed) is solved locally
 
 
 @dataclass
@@ -76,7 +79,7 @@ class Config:
     picard_tol: float = 1e-14
     picard_max: int = 16
     split: bool = True
-    picard_accel: bool = True    # per-particle secant relaxation of the Picard update (see step())
+    picard_accel: bool = True    # particle-local solves for creeping and slow particles (see step())
     quadrature: str = "closed"   # "closed" (Appendices A/B) or "gauss" (§4.7 split Gauss rule)
     nq: int = 16
     n0: float = 1.0              # ion background density (§5.4)
@@ -409,11 +412,28 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         rep = np.where(release, 0, rep)
         side = np.where(release, 0.0, side)
         u0, r0, u1, r1 = u1, r1, u2, r2
+    # a solve that ends on the landing of its nearest knot without reaching the tolerance: the
+    # root lies in the hair past the knot that the steps did not resolve, and the component
+    # slides there; its energy defect is then bounded by vbar_a = d H / dt times its residual,
+    # where it would otherwise be the particle's whole velocity times that residual
+    sl = sl | ((best_r > tol)[:, None] & (best_u == u_land))
     v_next[idx] = best_u
     if pinned is not None:
         slide |= pinned
     slide[idx] = sl
     return v_next, slide, local
+
+
+def slow_particles(v_it, v_prev, G):
+    """The plain-update particles whose iterate change did not shrink below SLOW_RATIO of the
+    previous one (max-norm over components, above SLOW_FLOOR of the particle's speed): their
+    own feedback is too strong for the outer iteration, as for orbits that cross a knot just
+    past their creeping range once the force jumps at knots grow.  They take the local solve
+    from then on.  A contracting outer loop (field-driven changes) shrinks every change far
+    faster than SLOW_RATIO, so it flags almost none."""
+    dnew = np.abs(G - v_it).max(axis=1)
+    dold = np.abs(v_it - v_prev).max(axis=1)
+    return (dnew > SLOW_RATIO * dold) & (dnew > SLOW_FLOOR * np.linalg.norm(v_it, axis=1))
 
 
 def j_scale(st, grid):
@@ -434,9 +454,13 @@ def step(st, cfg):
     converged = False
     slide = None
     crept = None
+    v_prev = None
     for p in range(cfg.picard_max + 1):
         it = picard_iteration(st, v_it, cfg, grid)
         if cfg.picard_accel:
+            if v_prev is not None:
+                slow = slow_particles(v_it, v_prev, it["v_new"])
+                crept = slow if crept is None else crept | slow
             v_next, slide, crept = local_solve(st, v_it, it, cfg, grid, slide, crept)
         else:
             v_next, slide = it["v_new"], None
@@ -451,6 +475,7 @@ def step(st, cfg):
         if e_v <= cfg.picard_tol and e_J <= cfg.picard_tol:
             converged = True
             break
+        v_prev = v_it
         v_it = v_next
         J_prev = it["J"]
     info = {"converged": converged, "iterations": len(hist), "errors": hist}

@@ -596,12 +596,15 @@ __global__ void k_first_scatter(StepParams p, const double* __restrict__ xi, con
 
 // Constants of the particle-local solve for "creeping" particles (see k_local); the
 // classifier is_creeping and its BETA_CREEP / D_KNOT live in pic_device.cuh.
-constexpr int LOCAL_STEPS = 24;      // push evaluations per creeping particle
+constexpr int LOCAL_STEPS = 32;      // push evaluations per creeping particle
 constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
 constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
 constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes SLIDE_PROBE short of the knot
 constexpr double SLIDE_FAR = 64.0;    // ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it
 constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
+constexpr double SLOW_RATIO = 0.25;   // a plain particle whose change did not shrink below this
+constexpr double SLOW_FLOOR = 1e-12;  // of the previous one (and exceeds this x its speed) is
+                                      // solved locally from then on
 
 struct PushOut {
     double Pw[3], xe[3], Ae[3], vw[3];
@@ -698,31 +701,53 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
             if (o.nseg < 0) atomicOr(status, DEV_ERR_SEGMENTS);
             pieces_push += (double)o.nseg;
             if (!(isfinite(o.vw[0]) && isfinite(o.vw[1]) && isfinite(o.vw[2]))) atomicOr(status, DEV_ERR_NONFINITE);
+            if constexpr (COMMIT) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
+                for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];
+            }
             if constexpr (!COMMIT) {
-                double beta_it[3], wv[3], bet2[3], dnum = 0.0, dden = 0.0;
+                double beta_it[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    double d = o.vw[a] - vi[a];   // change of the iterate, v^{p+1} - v^p
-                    dnum += d * d;
-                    dden += o.vw[a] * o.vw[a];
-                    beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
-                    double vb2 = 0.5 * (o.vw[a] + vn[a]);
-                    bet2[a] = p.dt * vb2 * p.invH[a];
-                    wv[a] = p.q_dV * vb2;
-                }
+                for (int a = 0; a < 3; ++a) beta_it[a] = p.dt * 0.5 * (vi[a] + vn[a]) * p.invH[a];
                 const double xk[3] = {x0[0] - p.koff, x0[1] - p.koff, x0[2] - p.koff};   // knot lattice
                 // a particle solved locally earlier in this step keeps the local solve, so that
                 // none alternates between it and the plain update
-                const bool creep = p.accel && (is_creeping(xk, beta_it) || (slide[i] & SLIDE_CREPT));
+                // So does one whose change did not shrink below SLOW_RATIO of the previous one: its
+                // own feedback is too strong for the outer iteration (orbits crossing a knot just
+                // past the creeping range, once the force jumps at knots grow).  A contracting
+                // outer loop shrinks field-driven changes far faster, so it flags almost none.
+                bool slow = false;
+                if (p.hist) {
+                    double dn = 0.0, dold = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        dn = fmax(dn, fabs(o.vw[a] - vi[a]));
+                        dold = fmax(dold, fabs(vi[a] - vnew[a * np + i]));   // v^p - v^{p-1}
+                    }
+                    const double spd = sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
+                    slow = dn > SLOW_RATIO * dold && dn > SLOW_FLOOR * spd;
+                }
+                const bool creep = p.accel && (is_creeping(xk, beta_it) || (slide[i] & SLIDE_CREPT) || slow);
                 if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
                 if (creep) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) vnew[a * np + i] = o.vw[a];   // G(v^p): the local solve starts there
                     if (!creep_flag) {
                         int k = atomicAdd(creep_count, 1);   // k_local solves it and adds its e_v terms
                         creep_list[k] = (int32_t)i;
                     }
                 } else {
+                    double wv[3], bet2[3], dnum = 0.0, dden = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vnew[a * np + i] = o.vw[a];
+                        const double d = o.vw[a] - vi[a];   // change of the iterate, v^{p+1} - v^p
+                        dnum += d * d;
+                        dden += o.vw[a] * o.vw[a];
+                        const double vb2 = 0.5 * (o.vw[a] + vn[a]);
+                        bet2[a] = p.dt * vb2 * p.invH[a];
+                        wv[a] = p.q_dV * vb2;
+                    }
                     ev_num += dnum;
                     ev_den += dden;
                     int ns = scatter_orbit<QUAD>(p, x0, bet2, wv, Jnext);
@@ -1061,7 +1086,16 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
             done = nstep >= LOCAL_STEPS - 1 || brs <= tol;
         }
         if (!done) continue;
-        // the particle's solve is over: its best iterate, sliding marks, e_v terms and current
+        // the particle's solve is over: its best iterate, sliding marks, e_v terms and current.
+        // A solve that ends on the landing of its nearest knot without reaching the tolerance:
+        // the root lies in the hair past the knot that the steps did not resolve, and the
+        // component slides there; its energy defect is then bounded by vbar_a = d H / dt times
+        // its residual, where it would otherwise be the whole velocity times that residual.
+        if (brs > tol) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (!sl[a] && bu[a] == uland[a]) sl[a] = true;
+        }
         uint8_t sb = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -1315,6 +1349,7 @@ StepParams make_params(const Ctx& c) {
     p.split = c.cfg.split_orbit_at_knots;
     p.nq = c.cfg.nq;
     p.accel = c.cfg.picard_accel;
+    p.hist = 0;
     p.order = c.cfg.shape_order;
     p.koff = (c.cfg.shape_order % 2 == 0) ? 0.5 : 0.0;
     p.det = c.cfg.deterministic;
@@ -1363,6 +1398,7 @@ void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null) {
 
 void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag) {
     StepParams p = make_params(c);
+    p.hist = !commit && c.cfg.picard_accel && c.run.hist;
     int nb = particle_blocks(c);
     const bool det = c.cfg.deterministic && !commit;
     const bool closed = c.cfg.quadrature == PIC_QUAD_CLOSED;

@@ -453,6 +453,7 @@ void step_begin(Ctx& c) {
     // PIC_MIXED: the iterations run in FP32 until they reach mixed_tol32 (or stop improving),
     // then in FP64 from the FP32 iterate.
     r.fp32 = c.cfg.precision == PIC_MIXED && np > 0;
+    r.began32 = r.fp32;
     cudaMemsetAsync(c.J[r.cur], 0, sizeof(double) * 3 * N, c.stream);
     {
         ProfScope ps(c, PH_SCATTER);
@@ -537,6 +538,7 @@ pic_status iter_finish(pic_ctx* ctx) {
                 launch_first_scatter(c, c.J[r.cur], c.vnew);   // also copies the iterate into vit
             }
             r.fp32 = false;
+            r.hist = false;
         }
     } else {
         if (c.prof) {
@@ -568,6 +570,11 @@ pic_status iter_finish(pic_ctx* ctx) {
             return PIC_OK;
         }
         std::swap(c.vit, c.vnew);
+        // vnew now holds v^p, the iterate before the next one.  After an FP32 phase the first
+        // FP64 change is the FP32 rounding of each particle, not its own contraction: the
+        // slow-particle test starts one FP64 iteration later.
+        ++r.p64;
+        r.hist = r.p64 >= (r.began32 ? 2 : 1);
         r.rotate();
     }
     if (r.p == c.cfg.picard_max) {   // the last iteration ran in FP32
@@ -1048,6 +1055,7 @@ pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push
         cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);
         launch_first_scatter(c, c.J[0], nullptr);
         mesh_phase(c, c.J[0], nullptr);
+        c.run.hist = false;   // scratch timing: no iterate history
         const int cand[4] = {2, 4, 8, 16};
         float best = INFINITY;
         int best_bps = c.push_bps;

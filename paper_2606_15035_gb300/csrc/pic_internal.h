@@ -58,6 +58,7 @@ struct StepParams {
     int split;                 // split orbits at knots
     int nq;                    // Gauss points (Gauss quadrature only)
     int accel;                 // particle-local solves for creeping particles
+    int hist;                  // vnew holds v^{p-1} (slow particles are found against it)
     int order;                 // B-spline degree r of the shape (1, 2, 3)
     double koff;               // knot offset: 0 (odd r, knots at the integers) or 0.5 (even r)
     int det;                   // deterministic mode: deposits go to acc (exact, order independent)
@@ -71,6 +72,9 @@ constexpr int FFT_MAX_STAGES = 16;
 struct StepRun {
     int cur = 0, prev = 1, next = 2;   // J buffers: current iterate, previous, next
     bool fp32 = false;                 // the next iteration runs in FP32 (PIC_MIXED)
+    bool hist = false;                 // vnew holds the previous FP64 iterate v^{p-1}
+    bool began32 = false;              // the step began with FP32 iterations (PIC_MIXED)
+    int p64 = 0;                       // FP64 iterations done in this step
     bool iterating = true;             // the Picard loop is still running
     bool converged = false;
     int p = 0, p32 = 0;                // iteration index, FP32 iterations done

@@ -325,6 +325,30 @@ def test_local_solves_match_oracle_where_plain_picard_cycles(sim):
     s.close()
 
 
+@pytest.mark.parametrize("seed,far,amp", [(5, 0.01, 0.05), (6, 0.05, 0.2)])
+def test_local_solves_near_knots_match_oracle(sim, seed, far, amp):
+    """Beams through a strong vector potential, particles 1e-12..1e-3 cells short of a knot and
+    drifting onto it: the knot-aware local solves (splits at landings, the knot-piece model
+    step, sliding within D_KNOT) give the oracle's step, and the energy stays at roundoff."""
+    from test_oracle_local_solve import _strong_A_knot_state
+    o, ocfg = _strong_A_knot_state(seed, far, amp)
+    x = opic.positions(o, ocfg)
+    cfg = sim.pic_config_default(n=ocfg.n, L=ocfg.L, dt=ocfg.dt, picard_tol=ocfg.picard_tol,
+                                 picard_max=ocfg.picard_max, diagnostics=1)
+    s = sim.PicSim(cfg, x, o.v, o.q, o.m)
+    st = s.get_state()
+    st.x, st.v, st.P, st.vprev = x, o.v, o.P, o.vprev
+    st.phi, st.psi, st.A, st.U, st.rho = o.phi, o.psi, o.A, o.U, o.rho
+    s.set_state(st)
+    E0 = s.energy().total
+    info = s.step(1)
+    o1, oinfo = opic.step(o, ocfg)
+    assert info.converged and oinfo["converged"]
+    compare_state(s.get_state(), o1, ocfg, 1e-12, ocfg.L)
+    assert abs(s.diagnostics().R_total) <= 1e-14 * E0
+    s.close()
+
+
 def test_mixed_precision_steps_match_fp64_oracle(sim):
     """PIC_MIXED: FP32 iterations then FP64 refinement to the same tolerance; the accepted
     step solves the FP64 discrete equations, so it matches the FP64 oracle."""

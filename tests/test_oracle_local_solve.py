@@ -112,7 +112,7 @@ def _strong_A_knot_state(seed, far, amp, npart=512):
                                                 (5, 0.05, 0.01, 4e-15), (6, 0.01, 0.2, 1e-10)])
 def test_local_solve_near_knots_in_a_strong_vector_potential(seed, far, amp, bound):
     """Every creeping particle is a root of its own equation or pinned onto its knot; at the
-    strongest potential (0.2, steep and strongly coupled) 24 evaluations do not always reach
+    strongest potential (0.2, steep and strongly coupled) LOCAL_STEPS evaluations do not always reach
     roundoff, and the bound is the one measured (2.4e-12) with margin, far below the 1e-2
     residuals the solve left before the knot-aware steps."""
     st, cfg = _strong_A_knot_state(seed, far, amp)
