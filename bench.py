@@ -47,9 +47,9 @@ SAMPLE_PARTICLES = 65536
 FLOPS_PER_PARTICLE = 190
 FLOPS_PER_PUSH_PIECE = 409
 FLOPS_PER_SCATTER_PIECE = 150
-# DRAM bytes (read + write) of one k_push launch on the 32^3 x 2.1M workload, from the ncu
-# capture summarised in profiles/k_push_fp64_twostream-32c-2M.md (this kernel version).
-KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 244.4e6}
+# DRAM bytes (read + write) of one k_push launch on the 32^3 x 2.1M workload, from an ncu
+# capture of this kernel version (dram__bytes_read.sum + dram__bytes_write.sum).
+KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 297.3e6}
 
 
 def parse():
