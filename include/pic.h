@@ -79,10 +79,12 @@ typedef struct {
     int32_t sort_every;           /* re-sort particles by cell every k steps (0: never) */
     int32_t diagnostics;          /* 1: accumulate the §5.1-§5.3 diagnostics during each step */
     int32_t accept_unconverged;   /* 1: commit a step that hit p_max (Algorithm 1 as printed) */
-    int32_t picard_accel;         /* 1: particles whose orbit crosses a knot on an axis where they
-                                     move < 0.1 cells get a particle-local solve of v = G_i(v)
-                                     with the iteration's fields fixed (an accelerated fixed point,
-                                     §4.8); all others, and every particle when 0, take the plain
+    int32_t picard_accel;         /* 1: particles whose orbit crosses (or nearly crosses) a knot on
+                                     an axis where they move < 0.1 cells, or whose iterate change
+                                     stopped shrinking below 1/4 of the previous one, get a
+                                     particle-local solve of v = G_i(v) with the iteration's fields
+                                     fixed (an accelerated fixed point, §4.8), for the rest of the
+                                     step; all others, and every particle when 0, take the plain
                                      update v^{p+1} = G(v^p) of Algorithm 1 */
     double helmholtz_tol;         /* accuracy of the CN Helmholtz solve (Chebyshev, central2): each
                                      mesh phase runs the fewest steps whose error bound is below
