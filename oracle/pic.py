@@ -61,6 +61,9 @@ D_KNOT = 1e-11        # cells: starting this close to a knot counts as creeping 
                       # margin: farther out the knot-piece step resolves the root)
 SLIDE_PROBE = 1e-12   # cells: the sliding test probes SLIDE_PROBE short of landing on the knot
 SLIDE_FAR = 64.0      # ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it (98% of that path beyond)
+D_FALLBACK = 1e-6     # cells: a failed solve slides the components that start this near a knot
+FAIL_RES = 1e-10      # failed: the best residual is above FAIL_RES x the particle's speed
+BETA_TRIAL = 1.0      # cells: the solve's trial orbits stay within this per axis
 LOCAL_STEPS = 32      # at most this many extra push evaluations per creeping particle
 LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
 OMEGA_MAX = 8.0       # bound on the secant step factor
@@ -330,7 +333,8 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
     r1 = Gf(u1) - u1
     r0 = np.where(sl, 0.0, r0)
     r1 = np.where(sl, 0.0, r1)
-    tol = LOCAL_TOL * np.maximum(np.linalg.norm(u0, axis=1), 1e-300)
+    speed = np.maximum(np.linalg.norm(u0, axis=1), 1e-300)
+    tol = LOCAL_TOL * speed
     # the best evaluation so far: the smallest largest-component |g| (all components of one
     # evaluation, since they are coupled; pinned components land on their knot)
     m0, m1 = np.abs(r0).max(axis=1), np.abs(r1).max(axis=1)
@@ -383,6 +387,10 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         u2 = np.where(br & np.isfinite(fp), fp, np.where(expand, u1 + fac * r1, u1 + sec * r1))
         u2 = np.where(split, u_split, u2)
         u2 = np.where(sl, u_land, u2)
+        # trial orbits stay within BETA_TRIAL cells per axis (the growing steps along g would
+        # otherwise leave the mesh neighbourhood a creeping particle can reach)
+        lim = BETA_TRIAL / c
+        u2 = np.clip(u2, -lim - vn, lim - vn)
         fac = np.where(expand, 2.0 * fac, fac)
         r2 = np.where(sl, 0.0, Gf(u2) - u2)
         m2 = np.abs(r2).max(axis=1)
@@ -412,11 +420,15 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         rep = np.where(release, 0, rep)
         side = np.where(release, 0.0, side)
         u0, r0, u1, r1 = u1, r1, u2, r2
-    # a solve that ends on the landing of its nearest knot without reaching the tolerance: the
-    # root lies in the hair past the knot that the steps did not resolve, and the component
-    # slides there; its energy defect is then bounded by vbar_a = d H / dt times its residual,
-    # where it would otherwise be the particle's whole velocity times that residual
-    sl = sl | ((best_r > tol)[:, None] & (best_u == u_land))
+    # A solve that ends above the tolerance on the landing of its nearest knot, or that fails
+    # (best residual above FAIL_RES of the speed) with a component starting within D_FALLBACK
+    # of a knot: that root lies in the hair past the knot that double precision (or the steps)
+    # did not resolve, and the component slides onto the knot.  Its energy defect is then
+    # bounded by vbar_a = d H / dt times its residual, where it would otherwise be the whole
+    # velocity times that residual; below FAIL_RES the residual itself costs less.
+    failed = best_r > FAIL_RES * speed
+    sl = sl | ((best_r > tol)[:, None] & (best_u == u_land)) | (failed[:, None] & (np.abs(d_knot) < D_FALLBACK))
+    best_u = np.where(sl, u_land, best_u)
     v_next[idx] = best_u
     if pinned is not None:
         slide |= pinned

@@ -601,6 +601,10 @@ constexpr double LOCAL_TOL = 1e-15;  // relative to the particle's speed
 constexpr double OMEGA_MAX = 8.0;    // bound on the secant step factor
 constexpr double SLIDE_PROBE = 1e-12; // cells: the sliding test probes SLIDE_PROBE short of the knot
 constexpr double SLIDE_FAR = 64.0;    // ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it
+constexpr double D_FALLBACK = 1e-6;   // cells: a failed solve slides the components that start
+                                      // this near a knot
+constexpr double FAIL_RES = 1e-10;    // failed: best residual above FAIL_RES x the speed
+constexpr double BETA_TRIAL = 1.0;    // cells: the solve's trial orbits stay within this per axis
 constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
 constexpr double SLOW_RATIO = 0.25;   // a plain particle whose change did not shrink below this
 constexpr double SLOW_FLOOR = 1e-12;  // of the previous one (and exceeds this x its speed) is
@@ -862,7 +866,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
     double ua[3], ga[3], ub[3], gb[3], side[3], fac[3], uland[3], dk[3], ue[3];
     bool brk[3], secok[3], sl[3], probe[3];
     int nrep[3];
-    double tol = 0.0, gm = 0.0, brs = 0.0;
+    double tol = 0.0, spd = 0.0, gm = 0.0, brs = 0.0;
     double nsolve = 0.0, neval = 0.0;
     while (true) {
         if (!active && !exhausted) {
@@ -897,7 +901,8 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                     sl[a] = (slide[i] >> a) & 1u;       // pinned earlier in this step: stays pinned
                     probe[a] = !sl[a] && fabs(dk[a]) < D_KNOT;
                 }
-                tol = LOCAL_TOL * fmax(sqrt(nrm), 1e-300);
+                spd = fmax(sqrt(nrm), 1e-300);
+                tol = LOCAL_TOL * spd;
                 paxis = 0;
                 while (paxis < 3 && !probe[paxis]) ++paxis;
                 phase = paxis < 3 ? 0 : 2;
@@ -979,6 +984,10 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                     } else {
                         ue[a] = u1[a] + sec * r1[a];         // secant while it converges
                     }
+                    // trial orbits stay within BETA_TRIAL cells per axis (the growing steps along g
+                    // would otherwise leave the neighbourhood a creeping particle can reach)
+                    const double lim = BETA_TRIAL / c;
+                    ue[a] = fmin(fmax(ue[a], -lim - vn[a]), lim - vn[a]);
                 }
             }
         }
@@ -1087,14 +1096,18 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
         }
         if (!done) continue;
         // the particle's solve is over: its best iterate, sliding marks, e_v terms and current.
-        // A solve that ends on the landing of its nearest knot without reaching the tolerance:
-        // the root lies in the hair past the knot that the steps did not resolve, and the
-        // component slides there; its energy defect is then bounded by vbar_a = d H / dt times
-        // its residual, where it would otherwise be the whole velocity times that residual.
-        if (brs > tol) {
+        // A solve that ends above the tolerance on the landing of its nearest knot, or that
+        // fails (best residual above FAIL_RES of the speed) with a component starting within
+        // D_FALLBACK of a knot: that root lies in the hair past the knot that double precision
+        // (or the steps) did not resolve, and the component slides onto the knot.  Its energy
+        // defect is then bounded by vbar_a = d H / dt times its residual, where it would
+        // otherwise be the whole velocity times that residual; below FAIL_RES the residual
+        // itself costs less.
+        {
+            const bool failed = brs > FAIL_RES * spd;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                if (!sl[a] && bu[a] == uland[a]) sl[a] = true;
+                if ((brs > tol && bu[a] == uland[a]) || (failed && fabs(dk[a]) < D_FALLBACK)) sl[a] = true;
         }
         uint8_t sb = 0;
 #pragma unroll
