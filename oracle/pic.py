@@ -63,7 +63,7 @@ SLIDE_PROBE = 1e-12   # cells: the sliding test probes SLIDE_PROBE short of land
 SLIDE_FAR = 64.0      # ... and max(SLIDE_PROBE, SLIDE_FAR |d|) past it (98% of that path beyond)
 D_FALLBACK = 1e-6     # cells: a failed solve slides the components that start this near a knot
 FAIL_RES = 1e-10      # failed: the best residual is above FAIL_RES x the particle's speed
-BETA_TRIAL = 1.0      # cells: the solve's trial orbits stay within this per axis
+BETA_TRIAL = 1.0      # cells: trial orbits stay within this beyond the iterate's own, per axis
 LOCAL_STEPS = 32      # at most this many extra push evaluations per creeping particle
 LOCAL_TOL = 1e-15     # local residual target, relative to the particle's speed
 OMEGA_MAX = 8.0       # bound on the secant step factor
@@ -348,6 +348,7 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
     rep = np.zeros(u0.shape, dtype=np.int64)          # consecutive replacements of one end
     c = cfg.dt * 0.5 / H                              # beta = c (u + v^n): orbit length in cells
     xk = x0 - koff                                    # start on the knot lattice
+    blim = np.abs(c * (u0 + vn)) + BETA_TRIAL         # bound on the trial orbits, per axis
     for _ in range(LOCAL_STEPS - 1):
         if np.all(best_r <= tol):
             break
@@ -387,10 +388,9 @@ def local_solve(st, v_it, it, cfg, grid, pinned=None, crept=None):
         u2 = np.where(br & np.isfinite(fp), fp, np.where(expand, u1 + fac * r1, u1 + sec * r1))
         u2 = np.where(split, u_split, u2)
         u2 = np.where(sl, u_land, u2)
-        # trial orbits stay within BETA_TRIAL cells per axis (the growing steps along g would
-        # otherwise leave the mesh neighbourhood a creeping particle can reach)
-        lim = BETA_TRIAL / c
-        u2 = np.clip(u2, -lim - vn, lim - vn)
+        # trial orbits stay within BETA_TRIAL cells beyond the iterate's own orbit, per axis
+        # (the growing steps along g would otherwise run past any neighbourhood of the root)
+        u2 = np.clip(u2, -blim / c - vn, blim / c - vn)
         fac = np.where(expand, 2.0 * fac, fac)
         r2 = np.where(sl, 0.0, Gf(u2) - u2)
         m2 = np.abs(r2).max(axis=1)

@@ -604,7 +604,8 @@ constexpr double SLIDE_FAR = 64.0;    // ... and max(SLIDE_PROBE, SLIDE_FAR |d|)
 constexpr double D_FALLBACK = 1e-6;   // cells: a failed solve slides the components that start
                                       // this near a knot
 constexpr double FAIL_RES = 1e-10;    // failed: best residual above FAIL_RES x the speed
-constexpr double BETA_TRIAL = 1.0;    // cells: the solve's trial orbits stay within this per axis
+constexpr double BETA_TRIAL = 1.0;    // cells: trial orbits stay within this beyond the iterate's
+                                      // own orbit, per axis
 constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
 constexpr double SLOW_RATIO = 0.25;   // a plain particle whose change did not shrink below this
 constexpr double SLOW_FLOOR = 1e-12;  // of the previous one (and exceeds this x its speed) is
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
     int64_t i = 0;
     int phase = 0, paxis = 0, nstep = 0;
     double x0[3], vn[3], Pn[3], u0[3], r0[3], u1[3], r1[3], bu[3];
-    double ua[3], ga[3], ub[3], gb[3], side[3], fac[3], uland[3], dk[3], ue[3];
+    double ua[3], ga[3], ub[3], gb[3], side[3], fac[3], uland[3], dk[3], ue[3], blim[3];
     bool brk[3], secok[3], sl[3], probe[3];
     int nrep[3];
     double tol = 0.0, spd = 0.0, gm = 0.0, brs = 0.0;
@@ -896,6 +897,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                     gsave[a * np + i] = u1[a];
                     r0[a] = u1[a] - u0[a];
                     nrm += u0[a] * u0[a];
+                    blim[a] = fabs(p.dt * 0.5 / p.H[a] * (u0[a] + vn[a])) + BETA_TRIAL;   // trial-orbit bound
                     dk[a] = rint(x0[a] - p.koff) - (x0[a] - p.koff);   // signed distance to the nearest knot
                     uland[a] = 2.0 * dk[a] * p.H[a] / p.dt - vn[a];
                     sl[a] = (slide[i] >> a) & 1u;       // pinned earlier in this step: stays pinned
@@ -984,10 +986,10 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
                     } else {
                         ue[a] = u1[a] + sec * r1[a];         // secant while it converges
                     }
-                    // trial orbits stay within BETA_TRIAL cells per axis (the growing steps along g
-                    // would otherwise leave the neighbourhood a creeping particle can reach)
-                    const double lim = BETA_TRIAL / c;
-                    ue[a] = fmin(fmax(ue[a], -lim - vn[a]), lim - vn[a]);
+                    // trial orbits stay within BETA_TRIAL cells beyond the iterate's own orbit, per
+                    // axis (the growing steps along g would otherwise run past any neighbourhood
+                    // of the root)
+                    ue[a] = fmin(fmax(ue[a], -blim[a] / c - vn[a]), blim[a] / c - vn[a]);
                 }
             }
         }
