@@ -253,8 +253,10 @@ pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
 
 /* Residual history of the last pic_step call (the last step it ran): for each Picard
- * iteration k, e_v[k] and e_J[k] (Algorithm 1's fixed-point errors, e_J = +inf at the first
- * iteration) and fp32[k] = 1 if the iteration ran in FP32 (PIC_MIXED), else 0.  Writes at
+ * iteration k, e_v[k] and e_J[k] (Algorithm 1's fixed-point errors of the update made by
+ * iteration k: ||v^{k+1} - v^k|| and the change of the orbit current between the two
+ * iterates, relative; FP32 iterations record the previous update's current change, +inf at
+ * the first) and fp32[k] = 1 if the iteration ran in FP32 (PIC_MIXED), else 0.  Writes at
  * most `cap` entries into each non-NULL array and returns the number of iterations (which
  * may exceed cap), or -1 for a NULL context. */
 int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32);

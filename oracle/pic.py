@@ -9,10 +9,11 @@ Readings of points the paper leaves open (each is listed in the design notes):
 * History velocity at the first step: v^{-1} := v^0, so the first guess is v^0.
 * Picard norms: e_v = ||v^{n+1,p+1} - v^{n+1,p}||_2 / ||v^{n+1,p+1}||_2 over all
   particles and components, v^{n+1,p+1} being the next iterate (G(v^{n+1,p}) itself for
-  plain Picard); e_J = ||J^p - J^{p-1}||_2 / (||J^p||_2 + J_scale) with
+  plain Picard); e_J = ||J(v^{n+1,p+1}) - J(v^{n+1,p})||_2 / (||J(v^{n+1,p+1})||_2 +
+  J_scale), the change of the orbit current made by the same update, with
   J_scale = sqrt(N_cells) * sum_i |q_i| |v_i^n| / |Omega| (a floor, because the
-  paired beams start with J ~ 0, §5.4); e_J is not defined at p = 0, so p = 0
-  never converges.  Converged when both are <= tau.
+  paired beams start with J ~ 0, §5.4).  Converged when both are <= tau; the current
+  of v^{n+1,p+1} is the one the final sweep then uses.
 * Final consistency sweep (§5.4): after convergence at iterate p, one more iteration
   is run from v^{n+1,p+1}; its current, fields, orbit integrals and particle state
   are the accepted step and feed the diagnostics.
@@ -162,17 +163,25 @@ def init(x, v, q, m, cfg):
 
 # --- Algorithm 1 ---------------------------------------------------------------------
 
-def picard_iteration(st, v_it, cfg, grid, diagnostics=False, slide=None):
-    """One pass of the Algorithm 1 loop body for the end-of-step velocity iterate ``v_it``."""
+def orbit_current(st, v_it, cfg, grid):
+    """The orbit current of the iterate v_it (Eq. (orbit-current)), split-path weights."""
     H = np.asarray(grid.H)
-    dt = cfg.dt
     vbar = 0.5 * (v_it + st.v)                       # orbit implied by the iterate
-    beta = dt * vbar / H                             # unwrapped displacement in cell units
-    # orbit current (Eq. (orbit-current)), split-path weights
+    beta = cfg.dt * vbar / H                         # unwrapped displacement in cell units
     J = np.zeros((3,) + grid.n)
     for sl in _chunks(st.xi.shape[0]):
         ow = orbit_weights(st.xi[sl], beta[sl], cfg, grid, with_gradient=False)
         J += orbit.deposit(st.q * vbar[sl], ow, grid)
+    return J
+
+
+def picard_iteration(st, v_it, cfg, grid, diagnostics=False, slide=None, J=None):
+    """One pass of the Algorithm 1 loop body for the end-of-step velocity iterate ``v_it``
+    (``J``: its orbit current, when already computed)."""
+    dt = cfg.dt
+    vbar = 0.5 * (v_it + st.v)                       # orbit implied by the iterate
+    if J is None:
+        J = orbit_current(st, v_it, cfg, grid)
     # continuity (Eq. (cn-continuity)) and CN potential solve (Eq. (cn-field-update))
     rho1 = mesh.continuity(st.rho, J, dt, grid)
     rho_half = 0.5 * (rho1 + st.rho)
@@ -460,7 +469,7 @@ def step(st, cfg):
     """
     grid = cfg.grid()
     v_it = 2.0 * st.v - st.vprev                     # extrapolated initial iterate
-    J_prev = None
+    J_it = None                                      # orbit current of v_it, once known
     jsc = j_scale(st, grid)
     hist = []
     converged = False
@@ -468,7 +477,7 @@ def step(st, cfg):
     crept = None
     v_prev = None
     for p in range(cfg.picard_max + 1):
-        it = picard_iteration(st, v_it, cfg, grid)
+        it = picard_iteration(st, v_it, cfg, grid, J=J_it)
         if cfg.picard_accel:
             if v_prev is not None:
                 slow = slow_particles(v_it, v_prev, it["v_new"])
@@ -478,18 +487,18 @@ def step(st, cfg):
             v_next, slide = it["v_new"], None
         vnorm = np.linalg.norm(v_next)
         e_v = np.linalg.norm(v_next - v_it) / vnorm if vnorm > 0 else 0.0   # no particles: no error
-        if J_prev is None:
-            e_J = np.inf
-        else:
-            num, den = np.linalg.norm(it["J"] - J_prev), np.linalg.norm(it["J"]) + jsc
-            e_J = num / den if den > 0 else (np.inf if num > 0 else 0.0)   # no current at all: no error
+        # the current fixed-point error of the same update v^p -> v^{p+1}: the orbit current of
+        # the new iterate (the one the next iteration, or the final sweep, uses) against J^p
+        J_next = orbit_current(st, v_next, cfg, grid)
+        num, den = np.linalg.norm(J_next - it["J"]), np.linalg.norm(J_next) + jsc
+        e_J = num / den if den > 0 else (np.inf if num > 0 else 0.0)       # no current at all: no error
         hist.append((float(e_v), float(e_J)))
         if e_v <= cfg.picard_tol and e_J <= cfg.picard_tol:
             converged = True
             break
         v_prev = v_it
         v_it = v_next
-        J_prev = it["J"]
+        J_it = J_next
     info = {"converged": converged, "iterations": len(hist), "errors": hist}
     if not converged:
         return st, info

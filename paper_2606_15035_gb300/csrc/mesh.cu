@@ -126,6 +126,23 @@ __global__ void k_source(MeshParams p, const double* __restrict__ J, const doubl
     put_partial(partials, S_EJ_DEN, den, sm, false);
 }
 
+// The current fixed-point error of one Picard update (Algorithm 1's convergence test):
+// partials of |J_new - J_old|^2 and |J_new|^2 over the 3 N mesh values, J_new being the orbit
+// current of the new iterate and J_old that of the iterate it was computed from.
+__global__ void k_jdiff(int64_t n3, const double* __restrict__ Jnew, const double* __restrict__ Jold,
+                        double* __restrict__ partials) {
+    __shared__ double sm[32];
+    double num = 0.0, den = 0.0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n3; g += (int64_t)gridDim.x * blockDim.x) {
+        const double j = Jnew[g];
+        const double d = j - Jold[g];
+        num += d * d;
+        den += j * j;
+    }
+    put_partial(partials, S_EJ_NUM, num, sm, false);
+    put_partial(partials, S_EJ_DEN, den, sm, false);
+}
+
 // One Chebyshev step on field blockIdx.y:  r = b - (c_id I - c_lap Delta_h) x,
 // d = alpha d + beta r,  x_out = x + d   (the three-term recurrence in its
 // "true residual" form, so rounding errors do not accumulate in r).
@@ -406,6 +423,11 @@ void launch_rhs0(Ctx& c) {
 void launch_source(Ctx& c, const double* Jcur, const double* Jprev) {
     k_source<<<mesh_blocks(c), THREADS, 0, c.stream>>>(mesh_params(c), Jcur, Jprev, c.rho0, c.rhs0, c.rho1, c.rhs,
                                                        c.partials);
+    ++c.launches;
+}
+
+void launch_jdiff(Ctx& c, const double* Jnew, const double* Jold) {
+    k_jdiff<<<mesh_blocks(c), THREADS, 0, c.stream>>>(3 * c.m.ncell, Jnew, Jold, c.partials);
     ++c.launches;
 }
 

@@ -491,6 +491,8 @@ void iter_issue(Ctx& c) {
             ProfScope ps(c, PH_LOCAL);
             launch_local(c, c.vit, c.vnew, c.J[r.next]);
         }
+        // the current fixed-point error of this update: J(v^{p+1}) against J(v^p)
+        launch_jdiff(c, c.J[r.next], c.J[r.cur]);
         launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
         if (c.cfg.picard_accel) launch_finalize(c, S_EVL_NUM, 2, local_blocks(c), false);
         launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
@@ -511,8 +513,12 @@ pic_status iter_finish(pic_ctx* ctx) {
     const double* h = c.host_results;
     if (r.p == 0) r.jscale = std::sqrt((double)N) * std::fabs(c.q) * h[S_JSCALE] / c.volume;
     {
+        // FP64 iterations: the change of the orbit current made by this update, J(v^{p+1})
+        // against J(v^p) (k_jdiff), the same update e_v measures.  FP32 iterations: the
+        // mesh phase's J^p against J^{p-1} (one update late; they stop on e_v alone).
         double num = std::sqrt(h[S_EJ_NUM]), den = std::sqrt(h[S_EJ_DEN]) + r.jscale;
-        r.e_J = r.p == 0 ? INFINITY : (den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0));
+        const double ej = den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0);
+        r.e_J = (r.fp32 && r.p == 0) ? INFINITY : ej;
     }
     if (r.fp32) {
         r.e_v = h[S_EV_DEN] > 0.0 ? std::sqrt(h[S_EV_NUM] / h[S_EV_DEN]) : 0.0;
@@ -521,8 +527,8 @@ pic_status iter_finish(pic_ctx* ctx) {
         c.hist_fp32.push_back(1);
         if (!std::isfinite(r.e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
         ++r.p32;
-        // e_J of iteration p measures the change that iteration p - 1 made to v, so e_v alone
-        // says that the FP32 iterate has reached the FP32 noise floor
+        // the FP32 iterations' e_J measures the change that iteration p - 1 made to v, so e_v
+        // alone says that the FP32 iterate has reached the FP32 noise floor
         const bool reached = r.e_v <= c.cfg.mixed_tol32;
         const bool stalled = r.p32 > 1 && r.e_v > 0.5 * r.e_v32_prev;
         r.e_v32_prev = r.e_v;

@@ -214,6 +214,8 @@ void launch_from32(Ctx& c, const float* a, double* b);
 // ---- launchers (mesh.cu) ----
 void launch_rhs0(Ctx& c);
 void launch_source(Ctx& c, const double* Jcur, const double* Jprev);
+// Partials of |Jnew - Jold|^2 and |Jnew|^2 (the current fixed-point error of one update).
+void launch_jdiff(Ctx& c, const double* Jnew, const double* Jold);
 void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nfields, int iters,
                       const double* alpha, const double* beta, double** x_io, double** x_spare);
 void launch_backsub_table(Ctx& c, bool diag);
