@@ -248,3 +248,19 @@ def test_relaxation_is_plain_picard_when_contracting():
     assert ia["iterations"] == ib["iterations"]
     # the gate may still fire on roundoff-level components, so agreement is to roundoff
     assert np.abs(a.v - b.v).max() <= 1e-15 * np.abs(b.v).max()
+
+
+def test_stopping_on_one_updates_errors_is_accurate_to_tolerance():
+    """Algorithm 1 stops once the current and velocity fixed-point errors of one update (v^p to
+    v^{p+1}) are below tau; the accepted step then agrees with a step solved far below tau
+    to tau's order, and its energy identity holds to roundoff."""
+    st, cfg = _c1_small(per_beam=4, tol=1e-13)
+    tight = pic.Config(n=cfg.n, L=cfg.L, dt=cfg.dt, picard_tol=1e-16, picard_max=40)
+    a, ia = pic.step(st, cfg)
+    b, ib = pic.step(st, tight)
+    assert ia["converged"] and ib["converged"] and ib["iterations"] > ia["iterations"]
+    for name in ("v", "P", "phi", "A"):
+        x, y = getattr(a, name), getattr(b, name)
+        assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y), name
+    E0 = sum(pic.energy(st, cfg))
+    assert abs(ia["R_total"]) <= 1e-14 * E0
