@@ -78,6 +78,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value, pg, device):
+    """The largest of one float over all ranks (the whole job's time is its slowest rank's), or
+    the value itself in a single-process run.  ``pg`` is torch.distributed (NCCL on the GPU
+    box, gloo in the CPU tests); ``device`` holds the reduction tensor."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, count, seconds):
+    """Whole-job throughput: the units all ranks processed, divided by the slowest rank's time."""
+    return units_per_rank * world * count / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -306,17 +323,13 @@ def main():
             pg.barrier()
         clk = sampler.stop() if sampler else None
         pr = sm.profile(False)
-        t_ms = ev0.elapsed_time(ev1)
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        if pg:
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
         drift_ = abs(sm.energy().total - e_start) / e_start
-        return sm, inf, pr, float(t.item()), drift_, clk
+        return sm, inf, pr, t_ms, drift_, clk
 
     s, info, prof, ms_max, drift, clocks = timed(args.precision, True)
     ms = ms_max
-    total_particles = w.n_particles * world
-    value = total_particles * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(w.n_particles, world, args.steps, ms_max / 1e3)
 
     # roofline of the dominant kernel (the fused push + scatter, FP64 ALU bound)
     pushes = prof.particle_pushes
@@ -366,11 +379,8 @@ def main():
             sim.pic_step(s.ctx, 1)
             sim.pic_get_state(s.ctx, view)        # step result: device -> host
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        t_t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        if pg:
-            pg.all_reduce(t_t, op=pg.ReduceOp.MAX)
-        e2e = {"value": total_particles * k_e2e / float(t_t.item()), "unit": UNIT,
+        t_e2e = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+        e2e = {"value": whole_job_rate(w.n_particles, world, k_e2e, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e,
                "what": "pic_set_state from pinned host + pic_step(1) + pic_get_state to pinned host, per step"}
 
@@ -385,7 +395,8 @@ def main():
         other = {
             "precision": "mixed: FP32 iterations (cell index + FP32 offsets), FP64 refinement to the same tau "
                          "and FP64 final sweep",
-            "value": total_particles * args.steps / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+            "value": whole_job_rate(w.n_particles, world, args.steps, ms2 / 1e3), "unit": UNIT,
+            "ms_per_step": ms2 / args.steps,
             "relative_energy_drift": drift2,
             "mean_picard_iterations": inf2.total_iterations / max(inf2.steps_done, 1),
             "mean_fp32_iterations": inf2.total_iterations_fp32 / max(inf2.steps_done, 1),
