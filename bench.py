@@ -1,20 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark of the GB300 PIC step: particle-steps per second, Picard iterations included.
+"""Benchmark of the GB300 PIC step: particle-steps per second, Picard iterations included,
+mixed precision against FP64 at the stated energy drift, with the rooflines of the particle
+kernels.
 
-Workload (one step = one full implicit time step: every Picard iteration of Algorithm 1
-plus the final consistency sweep, with the cell sort, the orbit-current scatters, the
-continuity + Crank--Nicolson mesh solves and the orbit pushes): the 3D periodic cold
-two-stream problem on a 32^3 mesh with 2,097,152 electrons (32 per beam per cell),
-beams +-0.2 c, thermal spread 1e-4, dt = 0.1, Picard tolerance 1e-13, FP64, split-orbit
-closed-form weights.  Synthetic, seeded inputs (pic_inputs).
+Default workload (the large two-stream configuration): the 3D periodic two-stream problem
+on a 128^3 mesh with 134,217,728 electrons (32 per beam per cell), beams +-0.2 c, thermal
+spread 1e-4, dt = 0.1, Picard tolerance 1e-13, split-orbit closed-form weights.  One step is
+one full implicit time step: every Picard iteration of Algorithm 1 plus the final
+consistency sweep, with the cell sort, the orbit-current scatters, the continuity +
+Crank--Nicolson mesh solves and the orbit pushes.  The headline is the mixed path (FP32
+Picard iterations, FP64 refinement to mixed_tol64 and the FP64 final sweep); the FP64 path
+runs on the same input beside it.  Synthetic, seeded inputs (pic_inputs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision mixed|fp64] [--probe-peaks]
 
 Multi-GPU runs (torchrun, one rank per GPU) are independent replicas with distinct
 seeds: the method is not sharded, so there is no data-path collective; only the timing
 barrier and the max-over-ranks reduction touch the process group.
 --impl reference times the FP64 CPU oracle (the reference arm of this benchmark) on a
-bounded sample of the same workload.
+bounded sample of the same workload, on all host cores (one independent sample per core).
 """
 
 from __future__ import annotations
@@ -33,23 +38,29 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "twostream-32c-2M"
+WORKLOAD = "twostream-128c-134M"
 METRIC = "particle-steps/s incl. Picard iters, mixed vs FP64 at stated energy drift; %HBM"
 UNIT = "particle-steps/s"
-# FP64 ALU peak of the GB300: 152 SMs x 2 FP64 FMA (4 flop) per clock per SM x 2070 MHz.
+MIXED_TOL64 = 1e-10       # FP64 refinement tolerance of the mixed path (energy error is second order in it)
+# FP64 ALU peak of the GB300: 152 SMs x 2 FP64 FMA (4 flop) per clock per SM x 2070 MHz (the
+# recipe's SM count and maximum clock; pic_probe_fma_rates measures the per-SM rate live).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
-SAMPLE_PARTICLES = 65536
-
+HBM_FALLBACK_GBS = 6800.0
+SUB_CELLS = 16            # the CPU oracle's sample: a periodic sub-box of SUB_CELLS^3 cells
+CPU_STEPS = 3             # timed oracle steps of the cpu_baseline leg
 
 # Algorithmic FP64 flops (add, mul = 1, FMA = 2; the scatter's atomic adds counted) of the
 # fused push + next-orbit scatter kernel, counted from the kernel source per particle and per
-# knot-free orbit piece (see the design notes):
+# knot-free orbit piece:
 FLOPS_PER_PARTICLE = 190
 FLOPS_PER_PUSH_PIECE = 409
 FLOPS_PER_SCATTER_PIECE = 150
-# DRAM bytes (read + write) of one k_push launch on the 32^3 x 2.1M workload, from an ncu
-# capture of this kernel version (dram__bytes_read.sum + dram__bytes_write.sum).
-KPUSH_TRAFFIC_BYTES = {"twostream-32c-2M": 297.3e6}
+# Bytes per particle-iteration of the FP32 push (read cell 4, offset 12, v^n 12, increment 12;
+# write the new increment 12).
+BYTES32_PER_PARTICLE = 52
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel version in the tree,
+# keyed by kernel and workload (None: not captured for this version).
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -59,15 +70,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--mixed-tol64", type=float, default=MIXED_TOL64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the other precision's run")
+    ap.add_argument("--no-mixed", action="store_true", help="alias of --no-other")
     ap.add_argument("--deterministic", action="store_true", help="bitwise reproducible mode")
     ap.add_argument("--ops", default="central2", choices=["central2", "spectral"],
                     help="spatial operators: central differences or the paper's spectral operators (FFT)")
     ap.add_argument("--shape-order", type=int, default=1, choices=[1, 2, 3],
                     help="B-spline degree r; r > 1 runs the split Gauss rule with 2 nq - 1 >= 3 r (FP64)")
+    ap.add_argument("--probe-peaks", action="store_true", help="print the measured FMA rates and exit")
     return ap.parse_args()
 
 
@@ -93,6 +107,17 @@ def max_over_ranks(value, pg, device):
 def whole_job_rate(units_per_rank, world, count, seconds):
     """Whole-job throughput: the units all ranks processed, divided by the slowest rank's time."""
     return units_per_rank * world * count / seconds
+
+
+def measured_peaks():
+    """HBM GB/s from the generated MEASURED_PEAKS.json, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s)"
 
 
 class ClockSampler:
@@ -145,24 +170,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(w, npart):
-    """A bounded sample of the workload for the CPU oracle: the same mesh, box and physics
-    with a strided subset of the particle pairs (charge rescaled to keep neutrality)."""
+# ---- the CPU oracle on a bounded sample (cpu_baseline and the reference arm) ------------------
+
+def oracle_sample(w, run=0):
+    """A bounded sample of workload ``w`` for the CPU oracle: a periodic sub-box of SUB_CELLS^3
+    cells with the workload's cell size (the whole mesh when it is that small), one particle per
+    beam per cell, the workload's beam speed, thermal spread, perturbation amplitude, dt and
+    Picard tolerance.  The oracle's cost per particle-step is that of the full workload: it is
+    dominated by the particle work (the mesh solve of 16^3 nodes is a few percent of it)."""
     import pic_inputs as pi
-    x, v, q, m = pi.workload_particles(w)
-    half = x.shape[0] // 2
-    stride = max(1, (2 * half) // npart)
-    pairs = np.arange(0, half, stride)[: npart // 2]
-    idx = np.concatenate([pairs, pairs + half])
-    scale = x.shape[0] / idx.size
-    return x[idx], v[idx], q * scale, m * scale
+    sub = tuple(min(SUB_CELLS, a) for a in w.n)
+    Ls = tuple(w.L[a] * sub[a] / w.n[a] for a in range(3))
+    x, v, q, m = pi.random_twostream(sub, Ls, 1, w.v0, w.eps, w.vth, w.seed + 50 + run)
+    return sub, Ls, x, v, q, m
 
 
-def time_oracle(w, npart, steps, warmup):
+def sample_text(w):
+    sub = tuple(min(SUB_CELLS, a) for a in w.n)
+    npart = 2 * sub[0] * sub[1] * sub[2]
+    return (f"{npart} particles in a periodic {sub[0]}x{sub[1]}x{sub[2]}-cell sub-box with the {w.name} cell size "
+            f"(1 per beam per cell; same beams, spread, dt, tau)")
+
+
+def time_oracle(name, steps, warmup, run=0):
+    """Oracle particle-steps/s over `steps` timed steps (after `warmup`) of one sample, one thread."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import pic_inputs as pi
     from oracle import pic as opic
-    x, v, q, m = oracle_sample(w, npart)
-    cfg = opic.Config(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max)
+    w = pi.WORKLOADS[name]
+    n, Ls, x, v, q, m = oracle_sample(w, run)
+    cfg = opic.Config(n=n, L=Ls, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max)
     st = opic.init(x, v, q, m, cfg)
     for _ in range(warmup):
         st, info = opic.step(st, cfg)
@@ -171,29 +208,64 @@ def time_oracle(w, npart, steps, warmup):
     for _ in range(steps):
         st, info = opic.step(st, cfg)
         iters += info["iterations"]
-    dt_s = time.perf_counter() - t0
-    return x.shape[0] * steps / dt_s, dt_s, iters / max(steps, 1), x.shape[0]
+    secs = time.perf_counter() - t0
+    return {"particles": int(x.shape[0]), "steps": steps, "secs": secs, "iterations": iters}
+
+
+def _oracle_worker(name, steps, warmup, run, queue):
+    queue.put(time_oracle(name, steps, warmup, run))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle_all_cores(name, steps, warmup):
+    """One independent oracle sample per host core (spawned processes, one numpy thread each),
+    all at once: throughput = all particle-steps over the slowest process's timed region."""
+    import multiprocessing as mp
+    cores = host_cores()
+    os.environ["OMP_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(name, steps, warmup, r, queue)) for r in range(cores)]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    secs = max(r["secs"] for r in res)
+    units = sum(r["particles"] * r["steps"] for r in res)
+    iters = sum(r["iterations"] for r in res) / max(sum(r["steps"] for r in res), 1)
+    return units / secs, secs, iters, cores
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle as it stands on all host cores, K timed steps of one
+    bounded sample per core after W warm-up steps (rank 0 only)."""
     import pic_inputs as pi
     if rank != 0:
         return
     w = pi.WORKLOADS[args.workload]
-    value, secs, mean_it, nsample = time_oracle(w, SAMPLE_PARTICLES, args.steps, args.warmup)
-    sample = (f"{nsample} particles (strided pairs of the {w.n_particles}-particle workload, same 32^3 mesh and "
-              f"physics), {args.steps} timed steps after {args.warmup} warm-up, numpy single thread")
+    value, secs, mean_it, cores = time_oracle_all_cores(w.name, args.steps, args.warmup)
+    sample = (f"per core: {sample_text(w)}; {cores} independent samples at once (one process per core, numpy "
+              f"single thread), {args.steps} timed steps after {args.warmup} warm-up")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "grid": list(w.n), "particles": nsample, "dt": w.dt,
-                   "picard_tol": w.picard_tol, "mean_picard_iterations": mean_it},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": w.name, "grid": list(w.n), "dt": w.dt, "picard_tol": w.picard_tol,
+                   "mean_picard_iterations": mean_it, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
+
+# ---- the GPU arm ------------------------------------------------------------------------------
 
 def run_ensemble(args, world, rank, local):
     """--workload ensemble-<R>: R independent runs (pic_inputs.ensemble_runs: meshes 16^3..48^3,
@@ -215,20 +287,26 @@ def run_ensemble(args, world, rank, local):
     for r in runs:
         x, v, q, m = pi.ensemble_particles(r)
         items.append((sim.pic_config_default(n=r.n, L=r.L, dt=r.dt, picard_tol=r.picard_tol, picard_max=r.picard_max,
-                                             precision=prec),
+                                             precision=prec, mixed_tol64=args.mixed_tol64 if prec else 0.0),
                       x, v, q, m))
     total = sum(r.n_particles for r in runs)
     ens = sim.PicEnsemble(items, autotune=True)
     e0 = [run.energy().total for run in ens.runs]
-    if args.warmup > 0:
-        ens.step(args.warmup)
+    drift = 0.0
+    for _ in range(args.warmup):
+        ens.step(1)
+        drift = max(drift, max(abs(run.energy().total - a) / a for run, a in zip(ens.runs, e0)))
     for run in ens.runs:
         run.profile(True)
     sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    infos, _ = ens.step(args.steps)
+    infos = []
+    for _ in range(args.steps):
+        inf, _ = ens.step(1)
+        infos.append(inf)
+        drift = max(drift, max(abs(run.energy().total - a) / a for run, a in zip(ens.runs, e0)))
     torch.cuda.synchronize()
     t_ens = time.perf_counter() - t0
     clk = sampler.stop()
@@ -240,38 +318,128 @@ def run_ensemble(args, world, rank, local):
         run.step(1)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    drift = max(abs(run.energy().total - a) / a for run, a in zip(ens.runs, e0))
-    iters = sum(i.total_iterations for i in infos) / max(sum(i.steps_done for i in infos), 1)
+    # end to end: every run's state through pinned host memory around each ensemble step
+    e2e = None
+    if not args.no_e2e:
+        from paper_2606_15035_gb300._lib import PicStateView
+        views, nbytes = [], 0
+        for run in ens.runs:
+            N = run.ncell
+            host = [torch.empty(3 * run.np, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+            host += [torch.empty(N, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+            host += [torch.empty(3 * N, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+            nbytes += sum(t.numel() * 8 for t in host)
+            view = PicStateView(*[t.data_ptr() for t in host], 0)
+            sim.pic_get_state(run.ctx, view)
+            views.append((view, host))
+        k_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            for run, (view, _) in zip(ens.runs, views):
+                sim.pic_set_state(run.ctx, view)
+            ens.step(1)
+            for run, (view, _) in zip(ens.runs, views):
+                sim.pic_get_state(run.ctx, view)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": whole_job_rate(total, world, k_e2e, t_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": k_e2e,
+               "what": "every run: pic_set_state from pinned host, then pic_ensemble_step(1), then pic_get_state"}
+    iters = sum(i.total_iterations for inf in infos for i in inf) / max(sum(i.steps_done for inf in infos for i in inf), 1)
     flops = sum(p.particle_pushes * FLOPS_PER_PARTICLE + p.push_pieces * FLOPS_PER_PUSH_PIECE +
                 p.scatter_pieces * FLOPS_PER_SCATTER_PIECE for p in profs)
+    push_ms = sum(p.push_ms for p in profs)
     tuning = sorted({tuple(t) for t in ens.tuning})
     ens.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pi.WORKLOADS["twostream-32c-2M"])
+        cpu["sample"] += " (the ensemble's runs have meshes of 16^3 to 48^3 cells at this cell size scale)"
     if rank != 0:
         return
     value = total * args.steps / t_ens
+    achieved = flops / (push_ms / 1e3) / 1e12 if push_ms > 0 else None
     line = {
         "metric": METRIC, "value": value * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_ens / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "runs": nruns, "particles_per_gpu": total,
                    "meshes": sorted({r.n[0] for r in runs}), "precision": args.precision,
-                   "mean_picard_iterations": iters, "relative_energy_drift_max": drift,
+                   "mixed_tol64": args.mixed_tol64 if prec else None,
+                   "mean_picard_iterations": iters, "relative_energy_drift": drift,
+                   "drift_definition": "max over runs and steps of |E^n - E^0| / E^0",
                    "timing": "host clock between device-wide synchronisations (runs on their own streams)",
                    "autotuned_blocks_per_sm (fp64, fp32)": tuning,
                    "l2": "inputs larger than L2"},
-        "roofline": {"bound": "alu", "achieved": flops / t_ens / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / t_ens / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_push (all runs, algorithmic flops over the whole timed region)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "kernel": "k_push (all runs; algorithmic flops over the summed k_push event durations)",
+                     "peak_note": "derived: 152 SMs x 4 flop/clk x 2070 MHz"},
         "sequential": {"value": total / t_seq, "unit": UNIT,
                        "what": "the same runs, one pic_step each, one after another"},
-        "cpu_baseline": None, "e2e": None,
+        "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(sum(p.launches for p in profs)), "clocks": clk,
     }
     print(json.dumps(line))
 
 
+def cpu_baseline(w):
+    """The oracle on bounded samples of workload w: CPU_STEPS timed steps on one core, then one
+    independent sample per host core at once."""
+    one = time_oracle(w.name, CPU_STEPS, 0)
+    v1 = one["particles"] * one["steps"] / one["secs"]
+    vall, secs, _, cores = time_oracle_all_cores(w.name, CPU_STEPS, 0)
+    return {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"per core: {sample_text(w)}, {CPU_STEPS} steps ({secs:.1f} s); {cores} samples at once, "
+                      f"one process per core, numpy single thread",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{sample_text(w)}, {CPU_STEPS} steps ({one['secs']:.1f} s)"}}
+
+
+def kernel_shares(prof, ms):
+    phases = {"k_push (FP64 iterations)": prof.push_ms, "k_push (FP64 final sweep)": prof.commit_ms,
+              "k_local": prof.local_ms, "k_push32": prof.push32_ms, "mesh phases": prof.mesh_ms,
+              "first scatters": prof.scatter_ms, "sort": prof.sort_ms}
+    return {k: v / ms for k, v in phases.items()} if ms > 0 else {}
+
+
+def fp64_push_roofline(prof, workload):
+    """k_push (FP64 push + next-orbit scatter) against the FP64 ALU peak."""
+    pushes = prof.particle_pushes
+    if not prof.push_launches or prof.push_ms <= 0:
+        return None
+    flops = (pushes * FLOPS_PER_PARTICLE + prof.push_pieces * FLOPS_PER_PUSH_PIECE
+             + prof.scatter_pieces * FLOPS_PER_SCATTER_PIECE)
+    achieved = flops / (prof.push_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(("k_push", workload)),
+            "traffic_unit": "DRAM bytes per launch (ncu dram read + write)",
+            "kernel": "k_push (fused FP64 orbit push + next-orbit current scatter, Picard iterations)",
+            "peak_note": "FP64 ALU, of derived: 152 SMs x 4 flop/clk x 2070 MHz (the live probe is in fma_probe)",
+            "launches": int(prof.push_launches), "ms_per_launch": prof.push_ms / prof.push_launches,
+            "flops_per_launch": flops / prof.push_launches,
+            "mean_orbit_pieces": prof.push_pieces / pushes if pushes else None}
+
+
+def fp32_push_roofline(prof, workload, npart, hbm_gbs, hbm_note):
+    """k_push32 (FP32 push + next-orbit scatter) against the HBM peak."""
+    if not prof.push32_launches or prof.push32_ms <= 0:
+        return None
+    bytes_per_launch = float(BYTES32_PER_PARTICLE) * npart
+    gbs = bytes_per_launch * prof.push32_launches / (prof.push32_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+            "traffic": NCU_TRAFFIC.get(("k_push32", workload)), "peak_note": hbm_note,
+            "kernel": "k_push32 (FP32 orbit push + next-orbit current scatter)",
+            "bytes_per_particle_iteration": BYTES32_PER_PARTICLE, "launches": int(prof.push32_launches),
+            "ms_per_launch": prof.push32_ms / prof.push32_launches,
+            "chunks_untiled": (prof.push32_chunks_global / prof.push32_chunks) if prof.push32_chunks else None}
+
+
 def main():
     args = parse()
+    if args.no_mixed:
+        args.no_other = True
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -287,6 +455,11 @@ def main():
     from paper_2606_15035_gb300._lib import PicStateView
 
     torch.cuda.set_device(local)
+    if args.probe_peaks:
+        f64, f32 = sim.pic_probe_fma_rates()
+        print(json.dumps({"fp64_fma_tflops": f64 / 1e12, "fp32_fma_tflops": f32 / 1e12,
+                          "fp64_derived_tflops": FP64_PEAK_TFLOPS, "device": torch.cuda.get_device_name()}))
+        return
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -295,18 +468,25 @@ def main():
     w = pi.WORKLOADS[args.workload]
     x, v, q, m = pi.workload_particles(w, run=rank)
     stream = torch.cuda.current_stream()
+    hbm_gbs, hbm_note = measured_peaks()
 
     def timed(precision, with_clocks):
-        """W warm-up steps, then K timed steps between barriers, CUDA events on the library's stream."""
+        """W warm-up steps, then K timed steps between barriers, CUDA events on the library's
+        stream; the total energy after every step (inside the timed region) gives the drift
+        max_n |E^n - E^0| / E^0 over all W + K steps."""
         extra = {"ops": 1 if args.ops == "spectral" else 0, "deterministic": int(args.deterministic)}
         if args.shape_order > 1:
             extra.update(shape_order=args.shape_order, quadrature=1, nq=(3 * args.shape_order + 2) // 2)
+        if precision == "mixed":
+            extra.update(precision=1, mixed_tol64=args.mixed_tol64)
         cfg = sim.pic_config_default(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max,
-                                     precision=1 if precision == "mixed" else 0, **extra)
+                                     **extra)
         sm = sim.PicSim(cfg, x, v, q, m)
-        e_start = sm.energy().total
-        if args.warmup > 0:
-            sm.step(args.warmup)
+        e0 = sm.energy().total
+        drift = 0.0
+        for _ in range(args.warmup):
+            sm.step(1)
+            drift = max(drift, abs(sm.energy().total - e0) / e0)
         sm.profile(True)                  # reset accumulators, profiling on
         sampler = ClockSampler(local) if with_clocks else None
         if sampler:
@@ -315,8 +495,14 @@ def main():
             pg.barrier()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        it = it32 = done = 0
         ev0.record(stream)
-        inf = sm.step(args.steps)
+        for _ in range(args.steps):
+            inf = sm.step(1)
+            it += inf.total_iterations
+            it32 += inf.total_iterations_fp32
+            done += inf.steps_done
+            drift = max(drift, abs(sm.energy().total - e0) / e0)
         ev1.record(stream)
         torch.cuda.synchronize()
         if pg:
@@ -324,38 +510,26 @@ def main():
         clk = sampler.stop() if sampler else None
         pr = sm.profile(False)
         t_ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
-        drift_ = abs(sm.energy().total - e_start) / e_start
-        return sm, inf, pr, t_ms, drift_, clk
+        return {"sim": sm, "prof": pr, "ms": t_ms, "drift": drift, "clocks": clk,
+                "iters": it / max(done, 1), "iters32": it32 / max(done, 1)}
 
-    s, info, prof, ms_max, drift, clocks = timed(args.precision, True)
-    ms = ms_max
-    value = whole_job_rate(w.n_particles, world, args.steps, ms_max / 1e3)
-
-    # roofline of the dominant kernel (the fused push + scatter, FP64 ALU bound)
-    pushes = prof.particle_pushes
-    flops = (pushes * FLOPS_PER_PARTICLE + prof.push_pieces * FLOPS_PER_PUSH_PIECE
-             + prof.scatter_pieces * FLOPS_PER_SCATTER_PIECE)
-    mean_pieces = prof.push_pieces / pushes if pushes else None
-    push_s = prof.push_ms / 1e3
-    achieved = flops / push_s / 1e12 if push_s > 0 else None
-    if args.shape_order > 1:
-        achieved = None   # the flop counts above are those of the linear closed forms
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": KPUSH_TRAFFIC_BYTES.get(w.name) if args.precision == "fp64" else None,
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "kernel": "k_push (fused orbit push + next-orbit current scatter, FP64)",
-                "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (derived; probe measured 1.203 TFLOP/s "
-                             "at 2010 MHz)",
-                "share_of_step": (prof.push_ms / ms) if ms > 0 else None,
-                "mean_orbit_pieces": mean_pieces}
-    # the particle-local solves of the creeping particles (their own kernel, after each push)
-    local = None
+    head = timed(args.precision, True)
+    s, prof, ms = head["sim"], head["prof"], head["ms"]
+    value = whole_job_rate(w.n_particles, world, args.steps, ms / 1e3)
+    shares = kernel_shares(prof, ms)
+    r64 = fp64_push_roofline(prof, w.name)
+    r32 = fp32_push_roofline(prof, w.name, w.n_particles, hbm_gbs, hbm_note)
+    # the dominant kernel of the step carries the roofline object
+    dominant = max(shares, key=shares.get) if shares else None
+    roofline = r32 if (dominant == "k_push32" and r32) else r64
+    if args.shape_order > 1 and roofline is r64 and roofline:
+        roofline = dict(roofline, achieved=None, frac=None)   # the flop counts are those of the linear closed forms
+    local_solves = None
     if prof.local_launches:
-        local = {"kernel": "k_local", "share_of_step": prof.local_ms / ms if ms > 0 else None,
-                 "ms_per_launch": prof.local_ms / prof.local_launches,
-                 "solves_per_launch": prof.local_solves / prof.local_launches,
-                 "evals_per_solve": prof.local_evals / prof.local_solves if prof.local_solves else None}
+        local_solves = {"kernel": "k_local", "share_of_step": prof.local_ms / ms if ms > 0 else None,
+                        "ms_per_launch": prof.local_ms / prof.local_launches,
+                        "solves_per_launch": prof.local_solves / prof.local_launches,
+                        "evals_per_solve": prof.local_evals / prof.local_solves if prof.local_solves else None}
 
     # end to end through the public API: the full state crosses host <-> device every step
     e2e = None
@@ -369,7 +543,7 @@ def main():
         view = PicStateView(*[host[k].data_ptr() for k in order], 0)
         sim.pic_get_state(s.ctx, view)
         nbytes = sum(t.numel() * 8 for t in host.values())
-        k_e2e = max(1, min(args.steps, 5))
+        k_e2e = max(1, min(args.steps, 3))
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -383,67 +557,66 @@ def main():
         e2e = {"value": whole_job_rate(w.n_particles, world, k_e2e, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k_e2e,
                "what": "pic_set_state from pinned host + pic_step(1) + pic_get_state to pinned host, per step"}
+        del host
+    s.close()
 
     # the other precision on the same workload ("mixed vs FP64 at stated energy drift")
     other = None
-    if args.precision == "fp64" and not args.no_mixed and args.shape_order == 1:
-        sm2, inf2, pr2, ms2, drift2, _ = timed("mixed", False)
-        sm2.close()
-        # per particle-iteration: read cell 4 + offset 12 + v^n 12 + increment 12, write 12
-        bytes32 = 52.0 * w.n_particles * pr2.push32_launches
-        hbm32 = bytes32 / (pr2.push32_ms / 1e3) / 1e9 if pr2.push32_ms > 0 else None
-        other = {
-            "precision": "mixed: FP32 iterations (cell index + FP32 offsets), FP64 refinement to the same tau "
-                         "and FP64 final sweep",
-            "value": whole_job_rate(w.n_particles, world, args.steps, ms2 / 1e3), "unit": UNIT,
-            "ms_per_step": ms2 / args.steps,
-            "relative_energy_drift": drift2,
-            "mean_picard_iterations": inf2.total_iterations / max(inf2.steps_done, 1),
-            "mean_fp32_iterations": inf2.total_iterations_fp32 / max(inf2.steps_done, 1),
-            "fp32_push_roofline": {"bound": "hbm", "achieved": hbm32, "peak": 6804.8, "unit": "GB/s",
-                                   "frac": (hbm32 / 6804.8) if hbm32 else None, "traffic": None,
-                                   "kernel": "k_push32 (FP32 orbit push + next-orbit scatter)",
-                                   "bytes_per_particle_iteration": 52},
-            "share_fp32_push": pr2.push32_ms / ms2 if ms2 > 0 else None,
-            "share_fp64_push": pr2.push_ms / ms2 if ms2 > 0 else None,
-        }
+    if not args.no_other and args.shape_order == 1:
+        oname = "fp64" if args.precision == "mixed" else "mixed"
+        o = timed(oname, False)
+        o["sim"].close()
+        po = o["prof"]
+        other = {"precision": oname, "value": whole_job_rate(w.n_particles, world, args.steps, o["ms"] / 1e3),
+                 "unit": UNIT, "ms_per_step": o["ms"] / args.steps, "relative_energy_drift": o["drift"],
+                 "mean_picard_iterations": o["iters"], "mean_fp32_iterations": o["iters32"],
+                 "kernel_shares": kernel_shares(po, o["ms"]),
+                 "fp64_push_roofline": fp64_push_roofline(po, w.name),
+                 "fp32_push_roofline": fp32_push_roofline(po, w.name, w.n_particles, hbm_gbs, hbm_note)}
+    fma = None
+    try:
+        f64, f32 = sim.pic_probe_fma_rates()
+        fma = {"fp64_tflops": f64 / 1e12, "fp32_tflops": f32 / 1e12, "what": "pic_probe_fma_rates, live"}
+    except Exception as e:  # the probe is evidence beside the derived peak, never a value
+        fma = {"error": str(e)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, secs, mit, nsample = time_oracle(w, SAMPLE_PARTICLES, 1, 0)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 step of {nsample} particles (strided pairs of the workload, same 32^3 mesh and physics), "
-                         f"{secs:.1f} s, numpy single thread"}
-    s.close()
+        cpu = cpu_baseline(w)
     if rank == 0:
+        mixed_desc = (f"mixed: FP32 Picard iterations (cell index + FP32 offsets), FP64 refinement to "
+                      f"e_v, e_J <= {args.mixed_tol64:g}, FP64 final sweep")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.n), "particles_per_gpu": w.n_particles, "dt": w.dt,
-                       "picard_tol": w.picard_tol,
-                       "precision": "fp64" if args.precision == "fp64" else
-                                    "mixed: FP32 iterations, FP64 refinement and final sweep",
+                       "picard_tol": w.picard_tol, "picard_max": w.picard_max,
+                       "precision": "fp64" if args.precision == "fp64" else mixed_desc,
                        "orbits": ("split at knots, closed form" if args.shape_order == 1 else
                                   f"split at the knots of the degree-{args.shape_order} B-spline, "
                                   f"{(3 * args.shape_order + 2) // 2}-point Gauss rule per piece"),
-                       "shape_order": args.shape_order,
-                       "ops": args.ops,
+                       "shape_order": args.shape_order, "ops": args.ops,
                        "deterministic": bool(args.deterministic),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": f"inputs larger than L2 (FP64 particle state {w.n_particles * 120 / 1e9:.1f} GB "
                              f"per GPU: x, v, P, v^(n-1), iterate)",
-                       "mean_picard_iterations": info.total_iterations / max(info.steps_done, 1),
-                       "mean_fp32_iterations": info.total_iterations_fp32 / max(info.steps_done, 1),
-                       "relative_energy_drift": drift},
+                       "mean_picard_iterations": head["iters"], "mean_fp32_iterations": head["iters32"],
+                       "relative_energy_drift": head["drift"],
+                       "drift_definition": "max over the W + K steps of |E^n - E^0| / E^0, E^0 at pic_init; "
+                                           "the energy is evaluated after every step, inside the timed region"},
             "roofline": roofline,
-            "local_solves": local,
+            "kernel_shares": shares,
+            "fp32_push_roofline": r32,
+            "local_solves": local_solves,
+            "fma_probe": fma,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(prof.launches),
-            "clocks": clocks,
-            "mixed": other,
+            "clocks": head["clocks"],
+            "other_precision": other,
+            "speedup_vs_other": (value / other["value"]) if other else None,
         }
         print(json.dumps(line))
     if pg:

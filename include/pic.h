@@ -111,6 +111,14 @@ typedef struct {
                                      symbol zero, Delta_h = -|k|^2; the CN update is then solved
                                      exactly per mode by FFT).  Spectral needs every n_a = 2^p 3^q
                                      <= 1024 */
+    double mixed_tol64;           /* PIC_MIXED: the FP64 iterations that follow the FP32 phase stop
+                                     once e_v and e_J are both <= this (0: picard_tol).  The step
+                                     is still closed by the FP64 final sweep from the accepted
+                                     iterate v*, so its energy error is the second-order product
+                                     (m / 2) sum_i (v_i^{n+1} - v_i^n) . (G(v*)_i - v*_i) of the
+                                     step's velocity change and the fixed-point residual (the
+                                     orbit's power balance and the field-energy balance hold
+                                     exactly for the orbit of v*, §4.6, §4.8) */
 } pic_config;
 
 #define PIC_OPS_CENTRAL2 0
@@ -203,6 +211,9 @@ typedef struct {
     double local_ms;             /* their summed event durations (not part of push_ms) */
     int64_t local_solves;        /* creeping particles solved by them */
     int64_t local_evals;         /* push evaluations those solves made (probes, first, iterations) */
+    int64_t push32_chunks;       /* chunks of 256 particles pushed by the FP32 push launches */
+    int64_t push32_chunks_global;/* ... of them whose orbits' mesh box exceeded the shared-memory
+                                    tile, so that they gathered and scattered in global memory */
 } pic_profile_t;
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
@@ -247,6 +258,27 @@ pic_status pic_get_positions(pic_ctx* ctx, double* xi, int32_t on_device);
  * G(v^{n+1,p}) (3 * np each, particles in pic_init order); their difference is each
  * particle's fixed-point residual (Algorithm 1).  PIC_ERR_ARG after a converged step. */
 pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t on_device);
+
+/* Right after a pic_step that committed its last step: the end-of-step velocity iterate
+ * v^{n+1,p+1} whose orbit that step's final consistency sweep used (Algorithm 1 and §5.4:
+ * x^{n+1} = x^n + dt (v^{n+1,p+1} + v^n) / 2 and P^{n+1} come from that orbit; the committed
+ * v^{n+1} is its image G(v^{n+1,p+1})), into v_iter (3 * np, pic_init order), and per
+ * particle the sliding bits of that step into slide (np bytes, pic_init order): bit a set
+ * means that component a landed exactly on a knot (the particle-local solve of picard_accel
+ * found no root that double precision resolves; the committed v_a is then the iterate's and
+ * P_a = m v_a + q A_h,a(x^{n+1})).  Either pointer may be NULL (not both).  Lets a caller
+ * check the accepted step against the method's own equations: G(v) = v within picard_tol
+ * for the components that do not slide.  PIC_ERR_ARG if no committed step precedes the call
+ * (a failed step, pic_set_state, pic_iterate or pic_autotune came after it). */
+pic_status pic_get_accepted(pic_ctx* ctx, double* v_iter, uint8_t* slide, int32_t on_device);
+
+/* Bound, in SM clock cycles, of each wait of the FP32 push (precision = PIC_MIXED) for the
+ * bulk copies that stage a chunk of particles in shared memory (default 2e9, about 1 s).
+ * When a wait runs out, the block records PIC_ERR_TIMEOUT, waits for its copies still in
+ * flight (always with the default bound, so that no copy lands after the block has exited)
+ * and stops; the step returns PIC_ERR_TIMEOUT and keeps the committed state.  A short bound
+ * is how a caller (or a test) checks that path without a fault.  PIC_ERR_ARG for cycles < 1. */
+pic_status pic_set_wait_limit(pic_ctx* ctx, int64_t cycles);
 
 /* Switch live profiling on (1) or off (0).  If `out` is non-NULL the accumulated profile is
  * copied there (after synchronising the stream) and the accumulators are reset. */
@@ -308,10 +340,13 @@ void pic_ensemble_destroy(pic_ensemble* e);
  * cudaMalloc where they need the update (a fixed, pre-committed device-memory budget, a
  * host thread that must not enter the CUDA allocator because it can synchronise the device,
  * or a plugin whose host application owns all device allocations).  It computes what
- * pic_step's mesh phase computes, (I - a Delta_h) F^{n+1} = (I + a Delta_h) F^n + dt W^n +
+ * pic_step's mesh phase computes with the central-difference operators (PIC_OPS_CENTRAL2
+ * only: Delta_h is the wide Laplacian sum_a D_a D_a; a context configured with
+ * PIC_OPS_SPECTRAL solves the same equations with the Fourier operators and gets a
+ * different update), (I - a Delta_h) F^{n+1} = (I + a Delta_h) F^n + dt W^n +
  * (dt^2 kappa^2 sigma / 2) src with a = kappa^2 dt^2 / 4 (src = rho_half for phi with sigma1,
- * J for A with sigma2), by the same Chebyshev iteration, then W^{n+1} = 2 (F^{n+1} - F^n) / dt
- * - W^n.
+ * J for A with sigma2), by the library's Chebyshev iteration (the fewest steps whose error
+ * bound is below helmholtz_tol, at most 1024), then W^{n+1} = 2 (F^{n+1} - F^n) / dt - W^n.
  *
  * Arguments: n, L: mesh nodes and box lengths (host); every array pointer is a DEVICE
  * pointer in the library's mesh layout (x-fastest; A, U, J component-major, 3 * ncell).
@@ -321,18 +356,27 @@ void pic_ensemble_destroy(pic_ensemble* e);
  *
  * Memory: working storage is one fixed __device__ array of 16 * PIC_STATIC_MAX_CELLS doubles
  * (4 MiB) that every device loading the library holds until the process exits; no call
- * allocates or frees device memory.  The first call on a device resolves that array's
- * device address (cudaGetSymbolAddress) with the device current, so make it before any
- * stream capture.  Every call on a device shares the array and nothing in it needs to start
- * at zero (each call writes what it reads), but two calls whose work overlaps on the GPU
- * (different streams, or before the earlier one finished) race on it.
+ * allocates or frees device memory.  Every call looks that array's address up on the current
+ * device (cudaGetSymbolAddress, which allocates nothing), so the address is never stale, even
+ * after a device reset; the first call on a device may load the library's device code there,
+ * so make it before any stream capture.  Every call on a device shares the array and nothing
+ * in it needs to start at zero (each call writes what it reads), but two calls whose work
+ * overlaps on the GPU (different streams, or before the earlier one finished) race on it.
  *
- * Errors: PIC_ERR_ARG for a null pointer, invalid sizes or constants, or
- * n0 * n1 * n2 > PIC_STATIC_MAX_CELLS; PIC_ERR_CUDA if a launch or the set-up fails. */
+ * Errors: PIC_ERR_ARG for a null pointer, invalid sizes or constants,
+ * n0 * n1 * n2 > PIC_STATIC_MAX_CELLS, or a helmholtz_tol that needs more than 1024 Chebyshev
+ * steps; PIC_ERR_CUDA if a launch or the address look-up fails. */
 pic_status pic_cn_update_static(const int32_t n[3], const double L[3], double dt, double kappa, double sigma1,
                                 double sigma2, double helmholtz_tol, const double* phi, const double* psi,
                                 const double* A, const double* U, const double* rho_half, const double* J,
                                 double* phi1, double* psi1, double* A1, double* U1, void* stream);
+
+/* Measured FMA throughput of the current device, in flop/s (an FMA counts 2): FP64 and FP32
+ * independent FMA chains over a grid of 16 blocks per SM, timed with CUDA events on `stream`
+ * after one warm-up launch.  The FP64 particle kernels are bound by the FP64 pipe, and their
+ * roofline divides by an arithmetic peak; this is the measurement behind it.  Synchronises the
+ * stream; makes one 8-byte stream-ordered allocation for the duration of the call. */
+pic_status pic_probe_fma_rates(void* stream, double* fp64_flops, double* fp32_flops);
 
 /* One-line description of the last error on this context ("" if none). */
 const char* pic_last_error(const pic_ctx* ctx);

@@ -31,8 +31,8 @@ PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 PIC_OPS_CENTRAL2, PIC_OPS_SPECTRAL = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
-            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_profile", "pic_residual_history",
-            "pic_cn_update_static", "pic_last_error", "pic_destroy", "pic_autotune", "pic_ensemble_init", "pic_ensemble_step",
+            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_get_accepted", "pic_set_wait_limit", "pic_profile", "pic_residual_history",
+            "pic_cn_update_static", "pic_probe_fma_rates", "pic_last_error", "pic_destroy", "pic_autotune", "pic_ensemble_init", "pic_ensemble_step",
             "pic_ensemble_size", "pic_ensemble_run", "pic_ensemble_last_error", "pic_ensemble_destroy"]
 
 
@@ -61,6 +61,7 @@ class PicConfig(C.Structure):
         ("deterministic", C.c_int32),
         ("shape_order", C.c_int32),
         ("ops", C.c_int32),
+        ("mixed_tol64", C.c_double),
     ]
 
 
@@ -153,6 +154,8 @@ class PicProfile(C.Structure):
         ("local_ms", C.c_double),
         ("local_solves", C.c_int64),
         ("local_evals", C.c_int64),
+        ("push32_chunks", C.c_int64),
+        ("push32_chunks_global", C.c_int64),
     ]
 
 
@@ -182,8 +185,11 @@ def lib():
     L.pic_residual_history.restype = C.c_int32
     L.pic_get_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    L.pic_get_accepted.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    L.pic_set_wait_limit.argtypes = [C.c_void_p, C.c_int64]
     L.pic_cn_update_static.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_double] + [C.c_void_p] * 10 + [C.c_void_p]
+    L.pic_probe_fma_rates.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
     L.pic_last_error.argtypes = [C.c_void_p]
     L.pic_last_error.restype = C.c_char_p
     L.pic_destroy.argtypes = [C.c_void_p]

@@ -8,20 +8,16 @@
 // file-scope __device__ array of fixed size, which every device that loads this library
 // holds until the process exits.
 #include <cmath>
-#include <mutex>
 
 #include "pic_internal.h"
 
 namespace {
 
 constexpr int64_t STATIC_MAX_CELLS = PIC_STATIC_MAX_CELLS;
+constexpr int STATIC_MAX_STEPS = 1024;   // Chebyshev steps one call may run
 
 // rhs | x (2 buffers) | d, 4 fields each.
 static __device__ __align__(256) double g_cn_scratch[4 * 4 * STATIC_MAX_CELLS];
-
-// Device address of g_cn_scratch per device, set up once per device with that device current.
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[256] = {nullptr};
 
 struct Dims {
     int n[3];
@@ -95,13 +91,13 @@ __global__ void k_static_backsub(Dims d, Fields4 F, Fields4 W, const double* __r
     }
 }
 
-int sin2_max_count(int n, double& mx) {
-    mx = 0.0;
+double sin2_max(int n) {
+    double mx = 0.0;
     for (int m = 0; m < n; ++m) {
-        double s = std::sin(2.0 * M_PI * m / n);
+        const double s = std::sin(2.0 * M_PI * m / n);
         mx = std::fmax(mx, s * s);
     }
-    return 0;
+    return mx;
 }
 
 }  // namespace
@@ -118,30 +114,6 @@ extern "C" pic_status pic_cn_update_static(const int32_t n[3], const double L[3]
     if (N > STATIC_MAX_CELLS) return PIC_ERR_ARG;     // beyond the fixed working storage
     if (!(dt > 0.0) || !(kappa > 0.0) || !(sigma1 > 0.0) || !(sigma2 > 0.0) || !(helmholtz_tol > 0.0))
         return PIC_ERR_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
-        cudaGetLastError();
-        return PIC_ERR_CUDA;
-    }
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
-            // The host-side name g_cn_scratch is not a device address: resolve it once per device.
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_cn_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
-                return PIC_ERR_CUDA;
-            }
-            g_scratch_ptr[dev] = (double*)p;
-        }
-        scratch = g_scratch_ptr[dev];
-    }
-    double* rhs = scratch;
-    double* xa = scratch + 4 * STATIC_MAX_CELLS;
-    double* xb = scratch + 8 * STATIC_MAX_CELLS;
-    double* dir = scratch + 12 * STATIC_MAX_CELLS;
-
     Dims d;
     d.N = N;
     double lmax = 1.0;
@@ -150,31 +122,33 @@ extern "C" pic_status pic_cn_update_static(const int32_t n[3], const double L[3]
         d.n[ax] = n[ax];
         const double H = L[ax] / n[ax];
         d.invH[ax] = 1.0 / H;
-        double mx;
-        sin2_max_count(n[ax], mx);
-        lmax += a * mx * d.invH[ax] * d.invH[ax];
+        lmax += a * sin2_max(n[ax]) * d.invH[ax] * d.invH[ax];
     }
-    // Chebyshev schedule on [1, lmax] to reach the error bound helmholtz_tol.
-    double alpha[1024], beta[1024];
-    int iters = 1;
-    {
-        const double theta = 0.5 * (lmax + 1.0), delta = 0.5 * (lmax - 1.0);
-        alpha[0] = 0.0;
-        beta[0] = 1.0 / theta;
-        if (delta > 1e-14 * theta) {
-            const double rho = (std::sqrt(lmax) - 1.0) / (std::sqrt(lmax) + 1.0);
-            iters = (int)std::ceil(std::log(2.0 / helmholtz_tol) / std::log(1.0 / rho)) + 1;
-            iters = iters < 1 ? 1 : (iters > 1024 ? 1024 : iters);
-            const double sigma = theta / delta;
-            double rprev = 1.0 / sigma;
-            for (int j = 1; j < iters; ++j) {
-                const double r = 1.0 / (2.0 * sigma - rprev);
-                alpha[j] = r * rprev;
-                beta[j] = 2.0 * r / delta;
-                rprev = r;
-            }
-        }
+    // Chebyshev schedule on the spectrum [1, lmax] of I - a Delta_h, the library's own
+    // (pic::cheb_schedule): the fewest steps whose error bound is below helmholtz_tol.
+    if (pic::cheb_steps(1.0, lmax, helmholtz_tol) > STATIC_MAX_STEPS) return PIC_ERR_ARG;
+    double alpha[STATIC_MAX_STEPS], beta[STATIC_MAX_STEPS];
+    const int iters = pic::cheb_schedule(1.0, lmax, helmholtz_tol, alpha, beta, STATIC_MAX_STEPS);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
     }
+    // The host-side name g_cn_scratch is a stand-in, not a device address.  Its address on the
+    // current device is looked up on every call, so that it is never stale (a device reset or
+    // a new primary context can move the module).
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_cn_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
+    }
+    double* scratch = static_cast<double*>(p);
+    double* rhs = scratch;
+    double* xa = scratch + 4 * STATIC_MAX_CELLS;
+    double* xb = scratch + 8 * STATIC_MAX_CELLS;
+    double* dir = scratch + 12 * STATIC_MAX_CELLS;
+
     cudaStream_t s = (cudaStream_t)stream;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

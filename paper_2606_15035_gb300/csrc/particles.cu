@@ -1566,6 +1566,18 @@ void launch_patch_local(Ctx& c, double* g) {
     ++c.launches;
 }
 
+// dst[id[i]] = the sliding bits (components 0..2) of particle i (device order -> caller order).
+__global__ void k_slide_out(int64_t np, const int64_t* __restrict__ id, const uint8_t* __restrict__ slide,
+                            uint8_t* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x)
+        dst[id[i]] = slide[i] & 7u;
+}
+
+void launch_slide_out(Ctx& c, uint8_t* dst) {
+    k_slide_out<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.id, c.slide, dst);
+    ++c.launches;
+}
+
 void launch_unpermute(Ctx& c, const double* src, double* dst, double s0, double s1, double s2) {
     k_unpermute<<<particle_blocks(c), THREADS, 0, c.stream>>>(c.np, c.id, src, dst, s0, s1, s2);
     ++c.launches;

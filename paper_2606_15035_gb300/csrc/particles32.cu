@@ -43,6 +43,7 @@ struct Params32 {
     int64_t stride;   // component stride of the FP32 particle arrays (a multiple of CHUNK32)
     int det;          // deterministic mode: FP64 deposits go to acc (exact, order independent)
     ExactAcc acc;
+    long long wait_cycles;   // bound of each wait for a chunk's bulk copies (SM clock cycles)
 };
 
 template <typename T>
@@ -431,7 +432,9 @@ __device__ __forceinline__ Chunk chunk_of(int64_t ch, int64_t np, int32_t ref_ce
 
 constexpr int NFIELD = 10;   // cell | offset (3) | v^n (3) | iterate increment (3)
 constexpr int F_CELL = 0, F_OFF = 1, F_V = 4, F_IT = 7;
-constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s: bound of every wait on a copy
+constexpr long long DRAIN_CYCLES = 2000000000LL;  // ~1 s: bound of the wait for the copies still in
+                                                  // flight when a block gives up (always the full bound,
+                                                  // so that no copy lands after the block has exited)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
@@ -467,7 +470,9 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+// Has phase `parity` of bar completed?  try_wait may suspend the thread for a while (until
+// the phase completes or a hardware time limit passes); test_wait returns at once.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -477,12 +482,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for phase `parity` of bar to complete; false after ~WAIT_CYCLES clocks.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of bar to complete; false once more than `limit` clocks have passed
+// without it.  The clock is read before every potentially suspending probe, so a limit
+// shorter than the copy's latency gives up at once instead of sleeping through it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
-    while (!mbar_test(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
+    while (true) {
+        if (mbar_poll(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
+        if (mbar_try(bar, parity)) return true;
+    }
 }
 
 // Bytes copied per field for chunk ch: the chunk's particles rounded up to 16 bytes (the
@@ -604,7 +623,7 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
     __syncthreads();
     if (tid == 0 && blockIdx.x < nchunks) stage_chunk(p, blockIdx.x, stage[0], &bar[0], cell, off, v32, vit32);
     float ev_num = 0.f, ev_den = 0.f;
-    int it = 0;
+    int it = 0, nchunk = 0, nglobal = 0;
     bool failed = false;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
         const int b = it & 1;
@@ -613,12 +632,13 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
             bulk_wait_read();      // the previous chunk's iterate store has left the other buffer
             stage_chunk(p, ch + gridDim.x, stage[b ^ 1], &bar[b ^ 1], cell, off, v32, vit32);
         }
-        if (!__syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1))) {
-            // a copy did not complete: report, let the copies in flight land, stop this block
+        if (!__syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1, p.wait_cycles))) {
+            // a copy did not complete in time: report, let the copies in flight land (with the
+            // full bound, whatever p.wait_cycles is), stop this block
             if (tid == 0) {
                 atomicOr(status, DEV_ERR_TIMEOUT);
-                mbar_wait(&bar[b], (it >> 1) & 1);
-                if (more) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1);
+                mbar_wait(&bar[b], (it >> 1) & 1, DRAIN_CYCLES);
+                if (more) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1, DRAIN_CYCLES);
             }
             failed = true;
             break;
@@ -650,6 +670,8 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
         float unused[3] = {0.f, 0.f, 0.f};
         const Box bx = block_box(lo, hi, unused, sbox);
         const bool tiled = bx.vol <= TILE_CAP;
+        ++nchunk;
+        nglobal += tiled ? 0 : 1;
         if (tiled) load_tile(bx, k.ref, p.m, table4, tab);
         __syncthreads();
         float bn[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
@@ -693,6 +715,10 @@ __global__ void __launch_bounds__(CHUNK32, PUSH32_MINB) k_push32(Params32 p, con
     if (failed) return;
     write_partial32<double>(partials, S_EV_NUM, (double)ev_num, sm);
     write_partial32<double>(partials, S_EV_DEN, (double)ev_den, sm);
+    if (threadIdx.x == 0) {
+        partials[S_CHUNKS32 * MAX_BLOCKS + blockIdx.x] = (double)nchunk;
+        partials[S_CHUNKS32_GLOBAL * MAX_BLOCKS + blockIdx.x] = (double)nglobal;
+    }
 }
 
 // FP64 gather table -> FP32 table (A^n, A^{n+1}, grad phi; 3 unused).
@@ -726,6 +752,7 @@ Params32 make_params32(const Ctx& c) {
     p.stride = c.np32;
     p.det = c.cfg.deterministic;
     p.acc = ExactAcc{c.acc_hi, c.acc_lo, c.inv_u_J, c.dev_status};
+    p.wait_cycles = c.wait_cycles;
     return p;
 }
 

@@ -70,9 +70,19 @@ void sin2_range(int n, double& mx, double& mn_pos) {
     }
 }
 
-// Chebyshev schedule for a symmetric operator with spectrum in [lmin, lmax]: the three-term
-// recurrence coefficients and the step count that brings the error bound
-// 2 rho^k / (1 + rho^{2k}), rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), below eps.
+}  // namespace
+
+namespace pic {
+
+int cheb_steps(double lmin, double lmax, double eps) {
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    if (delta <= 1e-14 * theta) return 1;
+    const double kap = lmax / lmin;
+    const double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    const double k = std::ceil(std::log(2.0 / eps) / std::log(1.0 / rho)) + 1.0;
+    return k > 1e9 ? 1000000000 : std::max(1, (int)k);
+}
+
 int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* beta, int cap) {
     double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
     if (delta <= 1e-14 * theta) {
@@ -80,10 +90,7 @@ int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* b
         beta[0] = 1.0 / theta;
         return 1;
     }
-    double kap = lmax / lmin;
-    double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
-    int k = (int)std::ceil(std::log(2.0 / eps) / std::log(1.0 / rho)) + 1;
-    k = std::min(std::max(k, 1), cap);
+    const int k = std::min(cheb_steps(lmin, lmax, eps), cap);
     double sigma = theta / delta;
     double rprev = 1.0 / sigma;
     alpha[0] = 0.0;
@@ -96,6 +103,10 @@ int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* b
     }
     return k;
 }
+
+}  // namespace pic
+
+namespace {
 
 pic_status check_cuda(pic_ctx* ctx, const char* where) {
     cudaError_t e = cudaGetLastError();
@@ -203,7 +214,7 @@ pic_status validate(const pic_config* cfg) {
     if (cfg->precision == PIC_MIXED) {
         if (cfg->quadrature != PIC_QUAD_CLOSED || cfg->n[0] > 1024 || cfg->n[1] > 1024 || cfg->n[2] > 1024)
             return PIC_ERR_ARG;
-        if (!(cfg->mixed_tol32 > 0.0) || cfg->mixed_max32 < 1) return PIC_ERR_ARG;
+        if (!(cfg->mixed_tol32 > 0.0) || cfg->mixed_max32 < 1 || !(cfg->mixed_tol64 >= 0.0)) return PIC_ERR_ARG;
     }
     if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
     if (cfg->shape_order < 1 || cfg->shape_order > 3) return PIC_ERR_ARG;
@@ -439,6 +450,10 @@ void step_begin(Ctx& c) {
     StepRun& r = c.run;
     const int64_t N = c.m.ncell, np = c.np;
     r = StepRun{};
+    // a device error of an earlier call (reported then) does not outlive it: the committed
+    // state was kept, so the context is usable again
+    cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
+    c.have_accepted = false;
     if (np > 0 && c.cfg.sort_every > 0 && c.steps % c.cfg.sort_every == 0) {
         ProfScope ps(c, PH_SORT);
         launch_sort(c);
@@ -481,6 +496,7 @@ void iter_issue(Ctx& c) {
         }
         launch_finalize(c, S_EV_NUM, 2, push32_blocks(c), false);
         launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
+        if (c.prof) launch_finalize(c, S_CHUNKS32, 2, push32_blocks(c), false);
     } else {
         cudaMemsetAsync(c.J[r.next], 0, sizeof(double) * 3 * N, c.stream);
         {
@@ -521,6 +537,10 @@ pic_status iter_finish(pic_ctx* ctx) {
         r.e_J = (r.fp32 && r.p == 0) ? INFINITY : ej;
     }
     if (r.fp32) {
+        if (c.prof) {
+            c.prof_acc.push32_chunks += (int64_t)h[S_CHUNKS32];
+            c.prof_acc.push32_chunks_global += (int64_t)h[S_CHUNKS32_GLOBAL];
+        }
         r.e_v = h[S_EV_DEN] > 0.0 ? std::sqrt(h[S_EV_NUM] / h[S_EV_DEN]) : 0.0;
         c.hist_ev.push_back(r.e_v);
         c.hist_eJ.push_back(r.e_J);
@@ -566,7 +586,9 @@ pic_status iter_finish(pic_ctx* ctx) {
         c.hist_fp32.push_back(0);
         if (!std::isfinite(r.e_v) || (r.p > 0 && !std::isfinite(r.e_J)))
             return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
-        if (r.e_v <= c.cfg.picard_tol && r.e_J <= c.cfg.picard_tol) {
+        // PIC_MIXED: the FP64 refinement that follows the FP32 phase stops at mixed_tol64
+        const double tol = (r.began32 && c.cfg.mixed_tol64 > 0.0) ? c.cfg.mixed_tol64 : c.cfg.picard_tol;
+        if (r.e_v <= tol && r.e_J <= tol) {
             r.converged = true;
             r.iterating = false;
             return PIC_OK;
@@ -651,6 +673,7 @@ void final_finish(Ctx& c) {
     std::swap(c.vprev, c.v);
     std::swap(c.v, c.vnew);
     c.steps += 1;
+    c.have_accepted = true;   // vit: the final sweep's iterate; slide: this step's sliding marks
     if (c.cfg.diagnostics) {
         const double* h = c.host_results;
         pic_diag_t& d = c.diag;
@@ -892,6 +915,7 @@ pic_status pic_set_state(pic_ctx* ctx, const pic_state_view* src) {
     cudaMemcpyAsync(c.W0 + N, src->U, sizeof(double) * 3 * N, kind, c.stream);
     cudaMemcpyAsync(c.rho0, src->rho, sizeof(double) * N, kind, c.stream);
     c.have_diag = false;
+    c.have_accepted = false;
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_set_state");
     return check_cuda(ctx, "pic_set_state");
 }
@@ -903,6 +927,8 @@ pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, co
     const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind kout = out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     double* vgiven = nullptr;
+    cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
+    c.have_accepted = false;   // vit and slide are overwritten below
     if (np > 0) {
         cudaMemcpyAsync(c.vnew, v_iter, sizeof(double) * 3 * np, kin, c.stream);
         launch_permute_in(c, c.vnew, c.sort_tmp, 1.0, 1.0, 1.0);   // caller order -> device order
@@ -968,6 +994,33 @@ pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t
     cudaMemcpyAsync(v_iter, c.sort_tmp, sizeof(double) * 3 * c.np, kind, c.stream);
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_iterate");
     return check_cuda(ctx, "pic_get_iterate");
+}
+
+pic_status pic_get_accepted(pic_ctx* ctx, double* v_iter, uint8_t* slide, int32_t on_device) {
+    if (!ctx || (!v_iter && !slide)) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.have_accepted)
+        return fail(ctx, PIC_ERR_ARG, "pic_get_accepted: only available right after a committed pic_step");
+    if (c.np == 0) return PIC_OK;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (v_iter) {
+        launch_unpermute(c, c.vit, c.sort_tmp, 1.0, 1.0, 1.0);
+        cudaMemcpyAsync(v_iter, c.sort_tmp, sizeof(double) * 3 * c.np, kind, c.stream);
+    }
+    if (slide) {
+        // the bytes go through the free scratch array sort_tmp (8 * 3 * np bytes >= np)
+        uint8_t* tmp = reinterpret_cast<uint8_t*>(c.sort_tmp);
+        launch_slide_out(c, tmp);
+        cudaMemcpyAsync(slide, tmp, (size_t)c.np, kind, c.stream);
+    }
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_accepted");
+    return check_cuda(ctx, "pic_get_accepted");
+}
+
+pic_status pic_set_wait_limit(pic_ctx* ctx, int64_t cycles) {
+    if (!ctx || cycles < 1) return PIC_ERR_ARG;
+    ctx->c.wait_cycles = (long long)cycles;
+    return PIC_OK;
 }
 
 pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out) {
@@ -1056,6 +1109,8 @@ pic_status pic_autotune(pic_ctx* ctx, int32_t* push_blocks_per_sm, int32_t* push
         // everything written is scratch (iterates, next current, creeping list), nothing of
         // the committed state changes.
         const int64_t N = c.m.ncell;
+        cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
+        c.have_accepted = false;   // the timing launches overwrite vit and slide
         mesh_begin(c);
         cudaMemcpyAsync(c.F1, c.F0, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, c.stream);
         cudaMemsetAsync(c.J[0], 0, sizeof(double) * 3 * N, c.stream);

@@ -42,6 +42,8 @@ enum Slot : int {
     S_PIECES_SCATTER,  // orbit pieces visited by the scatter of the next orbit (profiling)
     S_LOCAL_SOLVES,    // particle-local solves made by k_local (profiling)
     S_LOCAL_EVALS,     // push evaluations made by those solves (profiling)
+    S_CHUNKS32,        // particle chunks pushed by the FP32 push (profiling)
+    S_CHUNKS32_GLOBAL, // ... of which gathered and scattered through global memory (box too big)
     S_PROJ0,       // 8 null-mode projections (init)
     S_NULLSTAT = S_PROJ0 + 8,
     NSLOT
@@ -108,6 +110,9 @@ struct Ctx {
     const double *last_v = nullptr, *last_g = nullptr;   // last Picard iterate and the next one
     double* gsave = nullptr;         // G(v^p) of the locally solved particles (diagnostics)
     bool last_failed = false;        // the last step hit picard_max
+    bool have_accepted = false;      // vit and slide hold the last committed step's final-sweep
+                                     // iterate and sliding marks (until the next step begins)
+    long long wait_cycles = 2000000000LL;   // bound of k_push32's waits on its bulk copies
     uint8_t* slide = nullptr;        // per particle, bit a: component a slides along a knot
     int32_t* creep_list = nullptr;   // creeping particles of the current iteration (local solves)
     int* creep_count = nullptr;
@@ -190,6 +195,8 @@ void launch_local(Ctx& c, const double* vit, double* vnew, double* Jnext);
 void launch_kinetic(Ctx& c);
 void launch_unpermute(Ctx& c, const double* src_soa3, double* dst_soa3, double scale0, double scale1, double scale2);
 void launch_patch_local(Ctx& c, double* g);
+// dst[id[i]] = slide[i] & 7 (the sliding bits of each particle, in caller order).
+void launch_slide_out(Ctx& c, uint8_t* dst);
 void launch_permute_in(Ctx& c, const double* src_soa3, double* dst_soa3, double s0, double s1, double s2);
 void set_gauss_rule(int nq);
 
@@ -227,6 +234,13 @@ void launch_mesh_diag(Ctx& c, const double* Jfinal);
 void launch_finalize(Ctx& c, int slot0, int nslots, int nblocks, bool is_max);
 void launch_fill(Ctx& c, double* p, int64_t n, double value);
 void launch_scale_copy(Ctx& c, double* dst, const double* src, int64_t n, double s);
+
+// Chebyshev iteration for a symmetric operator with spectrum in [lmin, lmax] (pic_abi.cu):
+// cheb_steps is the step count that brings the error bound 2 rho^k / (1 + rho^{2k}),
+// rho = (sqrt(lmax / lmin) - 1) / (sqrt(lmax / lmin) + 1), below eps; cheb_schedule writes the
+// three-term recurrence coefficients of min(cheb_steps, cap) steps and returns that count.
+int cheb_steps(double lmin, double lmax, double eps);
+int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* beta, int cap);
 
 int particle_blocks(const Ctx& c);
 int local_blocks(const Ctx& c);

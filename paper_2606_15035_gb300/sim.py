@@ -171,11 +171,34 @@ def pic_get_iterate(ctx, npart):
     return a.reshape(3, npart).T.copy(), b.reshape(3, npart).T.copy()
 
 
+def pic_get_accepted(ctx, npart):
+    """The last committed step's final-sweep iterate v^{n+1,p+1} ((np, 3)) and its sliding
+    bits ((np,) uint8, bit a: component a landed on a knot), host arrays in pic_init order."""
+    a = np.zeros(3 * npart)
+    sl = np.zeros(max(npart, 1), dtype=np.uint8)
+    _check(_lib.lib().pic_get_accepted(ctx, _ptr(a), sl.ctypes.data, 0), ctx)
+    return a.reshape(3, npart).T.copy(), sl[:npart].copy()
+
+
+def pic_set_wait_limit(ctx, cycles: int):
+    _check(_lib.lib().pic_set_wait_limit(ctx, int(cycles)), ctx)
+
+
 def pic_get_positions(ctx, npart):
     """Positions in cell units exactly as stored, (np, 3) host array in pic_init order."""
     a = np.zeros(3 * npart)
     _check(_lib.lib().pic_get_positions(ctx, _ptr(a), 0), ctx)
     return a.reshape(3, npart).T.copy()
+
+
+def pic_probe_fma_rates(stream=None):
+    """Measured (FP64, FP32) FMA throughput of the current device in flop/s."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.lib().pic_probe_fma_rates(C.c_void_p(stream.cuda_stream), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def pic_last_error(ctx) -> str:
@@ -261,6 +284,13 @@ class PicSim:
 
     def last_iterate(self):
         return pic_get_iterate(self.ctx, self.np)
+
+    def accepted(self):
+        """(v^{n+1,p+1}, sliding bits) of the last committed step (pic_get_accepted)."""
+        return pic_get_accepted(self.ctx, self.np)
+
+    def set_wait_limit(self, cycles: int):
+        pic_set_wait_limit(self.ctx, cycles)
 
     def profile(self, enable=True, read=True):
         return pic_profile(self.ctx, enable, read)

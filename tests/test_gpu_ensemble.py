@@ -61,6 +61,36 @@ def test_ensemble_runs_match_the_same_runs_alone(sim):
     ens.close()
 
 
+def test_ensemble_members_match_the_oracle(sim):
+    """An FP64 member and a mixed member of the ensemble against the FP64 oracle after three
+    steps (the mixed path refines to the same tolerance in FP64, so it solves the same
+    equations): state within 1e-12 (FP64) and 1e-11 (mixed)."""
+    from oracle import pic as opic
+    runs = _runs(sim)
+    ens = sim.PicEnsemble(runs)
+    _, sts = ens.step(3)
+    assert sts == [0] * len(runs)
+    for k in (1, 2):                       # (6, 5, 4) FP64 and (12, 12, 12) mixed
+        cfg, x, v, q, m = runs[k]
+        n, L = tuple(cfg.n), tuple(cfg.L)
+        ocfg = opic.Config(n=n, L=L, dt=cfg.dt, picard_tol=cfg.picard_tol, picard_max=cfg.picard_max)
+        o = opic.init(x, v, q, m, ocfg)
+        for _ in range(3):
+            o, oinfo = opic.step(o, ocfg)
+            assert oinfo["converged"]
+        a = ens.runs[k].get_state()
+        tol = 1e-12 if cfg.precision == 0 else 1e-11
+        Lv = np.asarray(L)
+        d = a.x - opic.positions(o, ocfg)
+        assert np.abs((d + 0.5 * Lv) % Lv - 0.5 * Lv).max() <= tol * Lv.max()
+        for name in ("v", "P", "vprev", "phi", "psi", "A", "U", "rho"):
+            b = getattr(o, name)
+            scale = max(np.linalg.norm(b), 1e-14 * np.sqrt(b.size))
+            err = np.linalg.norm(getattr(a, name) - b) / scale
+            assert err <= tol, (k, name, err)
+    ens.close()
+
+
 def test_a_failing_run_does_not_stop_the_others(sim):
     # run 1 cannot converge (tolerance below roundoff, two iterations allowed)
     runs = _runs(sim, {1: dict(picard_tol=1e-30, picard_max=1)})

@@ -1,0 +1,208 @@
+"""GPU parity that does not depend on how the nonlinear solve reached its answer.
+
+§4.8 ties energy conservation to the converged discrete equations of Algorithm 1, not to
+the solver that converges them.  These tests therefore use the FP64 oracle only to
+*evaluate* Algorithm 1's map at the GPU's answer, never to solve:
+
+* take the GPU's committed level n (positions exactly as stored, velocities, momenta,
+  potentials, charge) and, after one GPU step, its accepted iterate v* (the end-of-step
+  velocity whose orbit the final consistency sweep used) and sliding marks
+  (pic_get_accepted);
+* run the oracle's Algorithm 1 body once from (level n, v*): orbit current J(v*),
+  continuity, Crank--Nicolson update, orbit gather, D_i A push, point gather, giving G(v*);
+* the GPU's committed level n+1 must be that body's output (the final sweep of §5.4), and
+  v* must be a fixed point of G: ||G(v*) - v*|| <= 2 tau ||v*|| over the components that
+  do not slide, with the current error ||J(G(v*)) - J(v*)|| within the same bound;
+* a sliding component (the particle-local solve found no root that double precision
+  resolves, a hair from a knot) must satisfy its own equations instead: the orbit lands
+  exactly on the knot, the committed v_a is the iterate's and P_a = m v_a + q A_h,a(x^{n+1}).
+
+Why 2 tau: the loop stops when ||v^{p+1} - v^p|| <= tau ||v^{p+1}|| and the current error
+is <= tau; v* = v^{p+1}, so G(v*) - v* = G(v^{p+1}) - G(v^p) for a plain update, the
+contraction (< 1) times a change below tau, and for a particle solved locally the change of
+its own root when the fields move from J(v^p) to J(v*), again bounded by the current error.
+The factor 2 covers the rounding of the two evaluations (~1e-16 relative).
+"""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import orbit as oorbit
+from oracle import pic as opic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim(cuda_ok):
+    from paper_2606_15035_gb300 import build
+    build.build()
+    from paper_2606_15035_gb300 import sim as s
+    return s
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+def pdiff(x, y, L):
+    L = np.asarray(L)
+    d = np.asarray(x) - np.asarray(y)
+    return np.abs((d + 0.5 * L) % L - 0.5 * L).max() if d.size else 0.0
+
+
+def oracle_level(s, q, m):
+    """The GPU's committed level as an oracle state: positions in cell units exactly as the
+    library stores them, everything else as copied out."""
+    st = s.get_state()
+    xi = s.positions_cells()
+    return opic.State(xi=xi, v=st.v, P=st.P, vprev=st.vprev, q=q, m=m, phi=st.phi, psi=st.psi, A=st.A, U=st.U,
+                      rho=st.rho)
+
+
+def check_accepted_step(s, o_n, ocfg, tau, state_tol=1e-12):
+    """One GPU step from the level o_n (already the context's state), checked against the
+    paper's equations evaluated by the oracle at the GPU's accepted iterate.  Returns
+    (relative fixed-point residual, number of sliding components)."""
+    info = s.step(1)
+    assert info.converged
+    v_star, bits = s.accepted()
+    new = s.get_state()
+    grid = ocfg.grid()
+    H = np.asarray(grid.H)
+    slide = np.stack([(bits >> a) & 1 for a in range(3)], axis=1).astype(bool)
+    it = opic.picard_iteration(o_n, v_star, ocfg, grid, slide=slide if slide.any() else None)
+    # the committed level n+1 is the final sweep's output from v*
+    assert rel(new.v, it["v_new"]) <= state_tol, ("v", rel(new.v, it["v_new"]))
+    assert rel(new.P, it["P"]) <= state_tol, ("P", rel(new.P, it["P"]))
+    assert pdiff(new.x, it["xi"] * H, ocfg.L) <= state_tol * max(ocfg.L)
+    for name in ("phi", "psi", "A", "U", "rho"):
+        a, b = getattr(new, name), it[name]
+        scale = max(np.linalg.norm(b), 1e-14 * np.sqrt(b.size))
+        assert np.linalg.norm(a - b) / scale <= state_tol, (name, np.linalg.norm(a - b) / scale)
+    # v* is a fixed point of Algorithm 1's map wherever it does not slide
+    G = opic.push_particles(o_n.xi, o_n.v, o_n.P, v_star, o_n.q, o_n.m, o_n.A, it["A"], it["gphi_half"],
+                            it["U_half"], ocfg, grid)["v_new"]
+    r = np.where(slide, 0.0, G - v_star)
+    vn = max(np.linalg.norm(v_star), 1e-300)
+    res = np.linalg.norm(r) / vn
+    assert res <= 2.0 * tau, ("fixed point", res, tau)
+    assert np.abs(r).max() <= 2.0 * tau * vn
+    # the current error of the same update: J(G(v*)) against J(v*)
+    J_next = opic.orbit_current(o_n, np.where(slide, v_star, G), ocfg, grid)
+    e_J = np.linalg.norm(J_next - it["J"]) / (np.linalg.norm(J_next) + opic.j_scale(o_n, grid))
+    assert e_J <= 2.0 * tau, ("current", e_J, tau)
+    # sliding components satisfy the sliding equations
+    if slide.any():
+        beta = ocfg.dt * 0.5 * (v_star + o_n.v) / H
+        end = o_n.xi + beta - oorbit.knot_offset(ocfg.order)
+        assert np.abs(end[slide] - np.rint(end[slide])).max() <= 1e-12          # lands on the knot
+        assert np.abs(beta[slide]).max() <= opic.D_FALLBACK                      # a hair from it
+        assert np.array_equal(new.v[slide], v_star[slide])
+        A_end = oorbit.point_gather(it["A"], it["xi"], grid, ocfg.order).T
+        Pa = o_n.m * new.v + o_n.q * A_end
+        assert np.abs(new.P[slide] - Pa[slide]).max() <= 1e-15 * np.abs(o_n.P).max()
+    return res, int(slide.sum())
+
+
+def make(sim, x, v, q, m, n, L, tau, dt=0.1, **kw):
+    cfg = sim.pic_config_default(n=n, L=L, dt=dt, picard_tol=tau, **kw)
+    okw = {}
+    if kw.get("ops") == 1:
+        okw["ops"] = "spectral"
+    if kw.get("quadrature") == 1:
+        okw.update(quadrature="gauss", nq=kw["nq"], order=kw.get("shape_order", 1),
+                   split=bool(kw.get("split_orbit_at_knots", 1)))
+    ocfg = opic.Config(n=n, L=L, dt=dt, picard_tol=tau, **okw)
+    return sim.PicSim(cfg, x, v, q, m), ocfg
+
+
+@pytest.mark.parametrize("accel,precision", [(1, 0), (0, 0), (1, 1)])
+def test_c1_run_is_a_fixed_point_of_algorithm1_every_step(sim, accel, precision):
+    """The 8^3 x 8192 cold two-stream workload for its 50 steps (tau = 1e-14 FP64; the mixed
+    path refines to the same tau), with and without the particle-local solves (accel = 0 is
+    Algorithm 1 as printed): every committed step is the oracle's final sweep from the GPU's
+    accepted iterate, which is a fixed point of the oracle's map."""
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.workload_particles(w)
+    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_accel=accel, precision=precision)
+    worst = 0.0
+    for k in range(w.steps):
+        o_n = oracle_level(s, q, m)
+        res, nslide = check_accepted_step(s, o_n, ocfg, w.picard_tol)
+        worst = max(worst, res)
+        assert nslide == 0 or accel == 1
+    assert worst <= 2.0 * w.picard_tol
+    s.close()
+
+
+@pytest.mark.parametrize("kind", ["spectral", "r2", "r3", "ragged"])
+def test_other_paths_are_fixed_points(sim, kind):
+    """The spectral operators, the degree-2 and -3 shapes (split Gauss rule) and a ragged mesh
+    with multi-knot orbits and starts exactly on knots: three steps each."""
+    if kind == "spectral":
+        n, L = (8, 8, 8), (1.2, 1.0, 0.9)
+        x, v, q, m = pi.random_twostream(n, L, 4, 0.25, 1e-2, 1e-2, 6008)
+        s, ocfg = make(sim, x, v, q, m, n, L, 1e-13, ops=1)
+    elif kind in ("r2", "r3"):
+        order = int(kind[1])
+        n, L = (6, 5, 5), (1.2, 1.0, 1.0)
+        x, v, q, m = pi.random_twostream(n, L, 2, 0.3, 1e-2, 2e-2, 5000 + order)
+        nq = (3 * order + 2) // 2
+        s, ocfg = make(sim, x, v, q, m, n, L, 1e-13, quadrature=1, nq=nq, shape_order=order)
+    else:
+        n, L = (5, 6, 7), (0.25, 0.3, 0.35)
+        H = np.asarray(L) / np.asarray(n)
+        x, v, q, m = pi.random_twostream(n, L, 3, 0.6, 1e-2, 0.05, 91)
+        x[:40] = np.round(x[:40] / H) * H % np.asarray(L)
+        s, ocfg = make(sim, x, v, q, m, n, L, 1e-13, dt=0.2)
+    for _ in range(3):
+        check_accepted_step(s, oracle_level(s, q, m), ocfg, 1e-13)
+    s.close()
+
+
+@pytest.mark.parametrize("seed,far,amp", [(5, 0.01, 0.05), (6, 0.05, 0.2), (7, 0.01, 0.01)])
+def test_near_knot_states_are_fixed_points_or_slide(sim, seed, far, amp):
+    """Particles 1e-12 .. 1e-3 cells short of a knot and drifting onto it, in a strong smooth
+    vector potential: the particle-local solves are busy and some components slide.  Every
+    non-sliding component is a fixed point of the oracle's map and every sliding one lands on
+    its knot with the canonical momentum of the sliding equations."""
+    from test_oracle_local_solve import _strong_A_knot_state
+    o, ocfg = _strong_A_knot_state(seed, far, amp)
+    ocfg = opic.replace(ocfg, picard_max=30)
+    x = opic.positions(o, ocfg)
+    cfg = sim.pic_config_default(n=ocfg.n, L=ocfg.L, dt=ocfg.dt, picard_tol=ocfg.picard_tol, picard_max=30)
+    s = sim.PicSim(cfg, x, o.v, o.q, o.m)
+    st = s.get_state()
+    st.x, st.v, st.P, st.vprev = x, o.v, o.P, o.vprev
+    st.phi, st.psi, st.A, st.U, st.rho = o.phi, o.psi, o.A, o.U, o.rho
+    s.set_state(st)
+    check_accepted_step(s, oracle_level(s, o.q, o.m), ocfg, ocfg.picard_tol)
+    s.close()
+
+
+def test_full_size_32c_steps_are_fixed_points(sim):
+    """The 32^3 x 2,097,152-particle workload (the benchmark's launch configuration), two
+    steps, each checked whole by one oracle evaluation of Algorithm 1's map."""
+    w = pi.WORKLOADS["twostream-32c-2M"]
+    x, v, q, m = pi.workload_particles(w)
+    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_max=w.picard_max)
+    for _ in range(2):
+        check_accepted_step(s, oracle_level(s, q, m), ocfg, w.picard_tol)
+    s.close()
+
+
+def test_accepted_iterate_needs_a_committed_step(sim):
+    x, v, q, m = pi.random_twostream((4, 4, 4), (1.0, 1.0, 1.0), 1, 0.2, 1e-3, 0.0, 31)
+    s, _ = make(sim, x, v, q, m, (4, 4, 4), (1.0, 1.0, 1.0), 1e-13)
+    with pytest.raises(sim.PicError) as e:
+        s.accepted()
+    assert e.value.status == 1
+    s.step(1)
+    s.accepted()
+    s.set_state(s.get_state())
+    with pytest.raises(sim.PicError):
+        s.accepted()
+    s.close()

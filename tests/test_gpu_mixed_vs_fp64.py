@@ -1,0 +1,73 @@
+"""The mixed-precision path against the FP64 GPU path, step by step, on the 128^3 mesh of the
+large two-stream configuration.
+
+Both contexts start from the same seeded state (beams +-0.2 c, thermal spread 1e-4,
+dt = 0.1, tau = 1e-13).  At 128^3 an orbit crosses 1.2 cells per step along the beams, so
+the mean orbit has more than two knot-free pieces, and with 16 particles per cell some
+chunks of 256 cell-sorted particles straddle two mesh rows: their mesh box no longer fits
+the FP32 push's shared-memory tile, and they take its global-memory path.  Both facts are
+checked from the library's own profile counters, so the test runs the code paths of the
+134M-particle run.
+
+Targets of the mixed path: state within 1e-5 of the FP64 path after every step, relative
+energy drift max_n |E^n - E^0| / E^0 <= 1e-9; FP64 path drift <= 1e-12.  The mixed path is
+run twice: refining in FP64 to tau, and to the looser mixed_tol64 = 1e-10 that the
+benchmark uses (its energy error per step is the product of the velocity change and the
+fixed-point residual, second order, so the drift bound still holds)."""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 20
+
+
+@pytest.fixture(scope="module")
+def sim(cuda_ok):
+    from paper_2606_15035_gb300 import build
+    build.build()
+    from paper_2606_15035_gb300 import sim as s
+    return s
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mixed_tol64", [0.0, 1e-10])
+def test_mixed_path_tracks_fp64_path_on_the_128_mesh(sim, mixed_tol64):
+    w = pi.WORKLOADS["twostream-128c-134M"]
+    x, v, q, m = pi.random_twostream(w.n, w.L, 8, w.v0, w.eps, w.vth, w.seed)     # 16 per cell, 33.5M
+    kw = dict(n=w.n, L=w.L, dt=w.dt, picard_tol=w.picard_tol, picard_max=w.picard_max)
+    a = sim.PicSim(sim.pic_config_default(**kw), x, v, q, m)
+    b = sim.PicSim(sim.pic_config_default(precision=1, mixed_tol64=mixed_tol64, **kw), x, v, q, m)
+    del x, v
+    a.profile(True)
+    b.profile(True)
+    e0a, e0b = a.energy().total, b.energy().total
+    assert abs(e0a - e0b) <= 1e-14 * e0a
+    drift_a = drift_b = 0.0
+    Lv = np.asarray(w.L)
+    for k in range(STEPS):
+        ia, ib = a.step(1), b.step(1)
+        assert ia.converged and ib.converged and ib.iterations_fp32 >= 1
+        drift_a = max(drift_a, abs(a.energy().total - e0a) / e0a)
+        drift_b = max(drift_b, abs(b.energy().total - e0b) / e0b)
+        if k % 5 == 4 or k == STEPS - 1:
+            sa, sb = a.get_state(), b.get_state()
+            d = sb.x - sa.x
+            assert np.abs((d + 0.5 * Lv) % Lv - 0.5 * Lv).max() <= 1e-5 * Lv.max()
+            for name in ("v", "P", "phi", "A", "psi", "U", "rho"):
+                err = rel(getattr(sb, name), getattr(sa, name))
+                assert err <= 1e-5, (k, name, err)
+            del sa, sb
+    pa, pb = a.profile(False), b.profile(False)
+    assert pa.push_pieces / pa.particle_pushes > 2.0                 # > 2 orbit pieces on average
+    assert pb.push32_chunks_global > 0 and pb.push32_chunks_global < pb.push32_chunks   # both FP32 paths
+    assert drift_a <= 1e-12, drift_a
+    assert drift_b <= 1e-9, drift_b
+    a.close()
+    b.close()

@@ -126,11 +126,13 @@ def test_steps_and_diagnostics_match_oracle(sim, accel):
     s.close()
 
 
-def test_full_c1_run_matches_oracle_after_50_steps(sim):
-    """The 8^3 x 8192 cold two-stream workload, FP64, dt = 0.1, 50 steps, tau = 1e-14."""
+@pytest.mark.parametrize("accel", [1, 0])
+def test_full_c1_run_matches_oracle_after_50_steps(sim, accel):
+    """The 8^3 x 8192 cold two-stream workload, FP64, dt = 0.1, 50 steps, tau = 1e-14; with
+    accel = 0 both sides run Algorithm 1 exactly as printed (plain Picard updates only)."""
     w = pi.WORKLOADS["twostream-8c-8k"]
     x, v, q, m = pi.workload_particles(w)
-    s, ocfg = pair(sim, x, v, q, m, w.n, w.L, dt=w.dt, tol=w.picard_tol)
+    s, ocfg = pair(sim, x, v, q, m, w.n, w.L, dt=w.dt, tol=w.picard_tol, picard_accel=accel)
     o = opic.init(x, v, q, m, ocfg)
     e0 = s.energy().total
     drift = 0.0
