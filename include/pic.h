@@ -119,6 +119,13 @@ typedef struct {
                                      step's velocity change and the fixed-point residual (the
                                      orbit's power balance and the field-energy balance hold
                                      exactly for the orbit of v*, §4.6, §4.8) */
+    int32_t mixed_pair_max;       /* PIC_MIXED: after the FP32 phase, at most this many refinement
+                                     iterations whose particle half (orbit integrals, gather, push,
+                                     next-orbit current) runs in FP32-pair arithmetic (two floats
+                                     per value, a 48-bit significand, on the FP32 pipes) before the
+                                     FP64 iterations; they stop early once e_v and e_J are <=
+                                     picard_tol or stop shrinking.  0: none (FP64 refinement from
+                                     the FP32 iterate).  Not used in deterministic mode */
 } pic_config;
 
 #define PIC_OPS_CENTRAL2 0
@@ -149,6 +156,8 @@ typedef struct {
     double e_v, e_J;      /* the last step's final velocity and current fixed-point errors */
     int32_t iterations_fp32;       /* of the last step's iterations, those run in FP32 (PIC_MIXED) */
     int32_t total_iterations_fp32; /* FP32 iterations summed over the committed steps */
+    int32_t iterations_pair;       /* of the last step's iterations, those run in FP32 pairs (PIC_MIXED) */
+    int32_t total_iterations_pair; /* FP32-pair iterations summed over the committed steps */
 } pic_step_info;
 
 typedef struct {
@@ -214,6 +223,8 @@ typedef struct {
     int64_t push32_chunks;       /* chunks of 256 particles pushed by the FP32 push launches */
     int64_t push32_chunks_global;/* ... of them whose orbits' mesh box exceeded the shared-memory
                                     tile, so that they gathered and scattered in global memory */
+    int64_t pushpair_launches;   /* FP32-pair push + scatter launches (PIC_MIXED refinement) */
+    double pushpair_ms;          /* their summed event durations */
 } pic_profile_t;
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
@@ -288,7 +299,8 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
  * iteration k, e_v[k] and e_J[k] (Algorithm 1's fixed-point errors of the update made by
  * iteration k: ||v^{k+1} - v^k|| and the change of the orbit current between the two
  * iterates, relative; FP32 iterations record the previous update's current change, +inf at
- * the first) and fp32[k] = 1 if the iteration ran in FP32 (PIC_MIXED), else 0.  Writes at
+ * the first) and fp32[k] = 1 if the iteration ran in FP32, 2 if its particle half ran in FP32
+ * pairs (PIC_MIXED), else 0 (FP64).  Writes at
  * most `cap` entries into each non-NULL array and returns the number of iterations (which
  * may exceed cap), or -1 for a NULL context. */
 int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32);

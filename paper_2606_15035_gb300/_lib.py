@@ -62,6 +62,7 @@ class PicConfig(C.Structure):
         ("shape_order", C.c_int32),
         ("ops", C.c_int32),
         ("mixed_tol64", C.c_double),
+        ("mixed_pair_max", C.c_int32),
     ]
 
 
@@ -94,6 +95,8 @@ class PicStepInfo(C.Structure):
         ("e_J", C.c_double),
         ("iterations_fp32", C.c_int32),
         ("total_iterations_fp32", C.c_int32),
+        ("iterations_pair", C.c_int32),
+        ("total_iterations_pair", C.c_int32),
     ]
 
 
@@ -156,6 +159,8 @@ class PicProfile(C.Structure):
         ("local_evals", C.c_int64),
         ("push32_chunks", C.c_int64),
         ("push32_chunks_global", C.c_int64),
+        ("pushpair_launches", C.c_int64),
+        ("pushpair_ms", C.c_double),
     ]
 
 

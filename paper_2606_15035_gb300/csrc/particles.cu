@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "pic_internal.h"
+#include "particle_common.cuh"
 
 namespace pic {
 
@@ -450,12 +451,6 @@ __device__ __forceinline__ void point_gather3(const StepParams& p, const double 
     for (int k = 0; k < 8; ++k) add(g[k], w[k], nullptr);
 }
 
-template <typename T>
-__device__ __forceinline__ void write_partial(double* partials, int slot, double v, double* sm, bool is_max) {
-    double r = is_max ? block_max(v, sm) : block_sum(v, sm);
-    if (threadIdx.x == 0) partials[slot * MAX_BLOCKS + blockIdx.x] = r;
-}
-
 // ---- kernels ----------------------------------------------------------------------
 
 __global__ void k_init_positions(StepParams p, const double* __restrict__ x, double* __restrict__ xi,
@@ -492,56 +487,6 @@ __global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, dou
             for (int k = 0; k < 8; ++k) dep(g[k], w[k], nullptr);
         }
     }
-}
-
-// Orbit-piece classes for ordering the particles of a chunk: 1, 2, 3, >= 4 pieces, and a
-// last class for the threads past the end of the particle array.
-constexpr int PIECE_CLASSES = 5;
-
-// Estimated number of pieces of an orbit x0 + s beta (1 + knots crossed), in FP32: only the
-// order of the work depends on it, never a result.
-__device__ __forceinline__ int piece_class_of(const StepParams& p, const double x0[3], const double beta[3]) {
-    int pieces = 1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float x = (float)(x0[a] - p.koff);
-        const float b = (float)beta[a];
-        pieces += abs((int)floorf(x + b) - (int)floorf(x));
-    }
-    return min(pieces, PIECE_CLASSES - 1) - 1;
-}
-
-// The same for particle j under the iterate vit.
-__device__ __forceinline__ int piece_class(const StepParams& p, const double* __restrict__ xi,
-                                           const double* __restrict__ v, const double* __restrict__ vit, int64_t j) {
-    const int64_t np = p.np;
-    double x0[3], beta[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        x0[a] = xi[a * np + j];
-        beta[a] = p.dt * 0.5 * (vit[a * np + j] + v[a * np + j]) * p.invH[a];
-    }
-    return piece_class_of(p, x0, beta);
-}
-
-// Position of this thread's item in the block when items are ordered by class (stable: equal
-// classes keep the thread order).  Uses wcount as scratch; ends with a barrier.
-__device__ __forceinline__ int stable_class_rank(int cls, int (*wcount)[PIECE_CLASSES]) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned mine = 0;
-#pragma unroll
-    for (int c = 0; c < PIECE_CLASSES; ++c) {
-        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
-        if (lane == 0) wcount[w][c] = __popc(m);
-        if (cls == c) mine = m;
-    }
-    __syncthreads();
-    int pos = __popc(mine & ((1u << lane) - 1u));
-    for (int c = 0; c < cls; ++c)
-        for (int v = 0; v < nw; ++v) pos += wcount[v][c];
-    for (int v = 0; v < w; ++v) pos += wcount[v][cls];
-    __syncthreads();
-    return pos;
 }
 
 // v^{n+1,0} = 2 v^n - v^{n-1} (Algorithm 1, extrapolated start) unless an iterate is given;
@@ -606,10 +551,6 @@ constexpr double D_FALLBACK = 1e-6;   // cells: a failed solve slides the compon
 constexpr double FAIL_RES = 1e-10;    // failed: best residual above FAIL_RES x the speed
 constexpr double BETA_TRIAL = 1.0;    // cells: trial orbits stay within this beyond the iterate's
                                       // own orbit, per axis
-constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
-constexpr double SLOW_RATIO = 0.25;   // a plain particle whose change did not shrink below this
-constexpr double SLOW_FLOOR = 1e-12;  // of the previous one (and exceeds this x its speed) is
-                                      // solved locally from then on
 
 struct PushOut {
     double Pw[3], xe[3], Ae[3], vw[3];
@@ -1348,6 +1289,8 @@ __global__ void k_permute_in(int64_t np, const int64_t* __restrict__ id, const d
     }
 }
 
+}  // namespace
+
 StepParams make_params(const Ctx& c) {
     StepParams p;
     p.m = c.m;
@@ -1371,8 +1314,6 @@ StepParams make_params(const Ctx& c) {
     p.acc = ExactAcc{c.acc_hi, c.acc_lo, c.inv_u_J, c.dev_status};
     return p;
 }
-
-}  // namespace
 
 int local_blocks(const Ctx& c) { return std::max(1, std::min(particle_blocks(c), c.sms * 2)); }
 

@@ -159,6 +159,7 @@ void prof_resolve(Ctx& c) {
             case PH_SORT: c.prof_acc.sort_ms += ms; break;
             case PH_PUSH32: c.prof_acc.push32_ms += ms; c.prof_acc.push32_launches += 1; break;
             case PH_LOCAL: c.prof_acc.local_ms += ms; c.prof_acc.local_launches += 1; break;
+            case PH_PUSHPAIR: c.prof_acc.pushpair_ms += ms; c.prof_acc.pushpair_launches += 1; break;
             default: break;
         }
         c.ev_pool.push_back(pe.second.first);
@@ -215,6 +216,7 @@ pic_status validate(const pic_config* cfg) {
         if (cfg->quadrature != PIC_QUAD_CLOSED || cfg->n[0] > 1024 || cfg->n[1] > 1024 || cfg->n[2] > 1024)
             return PIC_ERR_ARG;
         if (!(cfg->mixed_tol32 > 0.0) || cfg->mixed_max32 < 1 || !(cfg->mixed_tol64 >= 0.0)) return PIC_ERR_ARG;
+        if (cfg->mixed_pair_max < 0) return PIC_ERR_ARG;
     }
     if (!(cfg->helmholtz_tol > 0.0) || cfg->sort_every < 0) return PIC_ERR_ARG;
     if (cfg->shape_order < 1 || cfg->shape_order > 3) return PIC_ERR_ARG;
@@ -315,6 +317,7 @@ pic_status allocate(pic_ctx* ctx) {
             if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
                 return fail(ctx, PIC_ERR_ARG, "the allocator returned a pointer that is not 16-byte aligned");
         ALLOC(c.table32, float, 12 * N);
+        if (c.cfg.mixed_pair_max > 0 && !c.cfg.deterministic) ALLOC(c.table_pair, float, 20 * N);
     }
     if (c.cfg.deterministic) {
         ALLOC(c.acc_hi, long long, 3 * N);
@@ -499,7 +502,13 @@ void iter_issue(Ctx& c) {
         if (c.prof) launch_finalize(c, S_CHUNKS32, 2, push32_blocks(c), false);
     } else {
         cudaMemsetAsync(c.J[r.next], 0, sizeof(double) * 3 * N, c.stream);
-        {
+        r.pair_issued = r.pair;
+        if (r.pair) {
+            // PIC_MIXED refinement: the particle half in FP32 pairs from the pair table
+            launch_table_df(c);
+            ProfScope ps(c, PH_PUSHPAIR);
+            launch_push_df(c, c.vit, c.vnew, c.J[r.next]);
+        } else {
             ProfScope ps(c, PH_PUSH);
             launch_push(c, c.vit, c.vnew, c.J[r.next], false, false);
         }
@@ -565,6 +574,7 @@ pic_status iter_finish(pic_ctx* ctx) {
             }
             r.fp32 = false;
             r.hist = false;
+            r.pair = c.table_pair != nullptr;   // FP32-pair refinement next, if configured
         }
     } else {
         if (c.prof) {
@@ -583,12 +593,23 @@ pic_status iter_finish(pic_ctx* ctx) {
         r.e_v = den > 0.0 ? std::sqrt(num / den) : 0.0;
         c.hist_ev.push_back(r.e_v);
         c.hist_eJ.push_back(r.e_J);
-        c.hist_fp32.push_back(0);
+        c.hist_fp32.push_back(r.pair_issued ? 2 : 0);
         if (!std::isfinite(r.e_v) || (r.p > 0 && !std::isfinite(r.e_J)))
             return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
+        if (r.pair_issued) {
+            // An FP32-pair iteration never ends the step: the FP64 iterations that follow check
+            // the iterate in FP64.  The pair phase ends once its iterate meets picard_tol (its
+            // fixed point is the FP64 one to ~1e-15 of the speed), stops shrinking, or has run
+            // mixed_pair_max iterations.
+            ++r.ppair;
+            const bool met = r.e_v <= c.cfg.picard_tol && r.e_J <= c.cfg.picard_tol;
+            const bool stalled = r.ppair > 1 && r.e_v > 0.5 * r.e_vpair_prev;
+            r.e_vpair_prev = r.e_v;
+            if (met || stalled || r.ppair >= c.cfg.mixed_pair_max) r.pair = false;
+        }
         // PIC_MIXED: the FP64 refinement that follows the FP32 phase stops at mixed_tol64
         const double tol = (r.began32 && c.cfg.mixed_tol64 > 0.0) ? c.cfg.mixed_tol64 : c.cfg.picard_tol;
-        if (r.e_v <= tol && r.e_J <= tol) {
+        if (!r.pair_issued && r.e_v <= tol && r.e_J <= tol) {
             r.converged = true;
             r.iterating = false;
             return PIC_OK;
@@ -620,6 +641,7 @@ pic_status iter_close(pic_ctx* ctx, pic_step_info* last) {
     if (last) {
         last->iterations = std::min(r.p, c.cfg.picard_max) + 1;
         last->iterations_fp32 = r.p32;
+        last->iterations_pair = r.ppair;
         last->converged = r.converged ? 1 : 0;
         last->e_v = r.e_v;
         last->e_J = r.e_J;
@@ -749,6 +771,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->picard_accel = 1;
     cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
+    cfg->mixed_pair_max = 8;
     cfg->deterministic = 0;
     cfg->shape_order = 1;
     cfg->ops = PIC_OPS_CENTRAL2;
@@ -840,9 +863,11 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps, pic_step_info* info) {
         local.steps_done += 1;
         local.total_iterations += last.iterations;
         local.total_iterations_fp32 += last.iterations_fp32;
+        local.total_iterations_pair += last.iterations_pair;
     }
     local.iterations = last.iterations;
     local.iterations_fp32 = last.iterations_fp32;
+    local.iterations_pair = last.iterations_pair;
     local.converged = last.converged;
     local.e_v = last.e_v;
     local.e_J = last.e_J;
@@ -1265,6 +1290,7 @@ pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps, pic_step_info* inf
             acc[r].steps_done += 1;
             acc[r].total_iterations += last[r].iterations;
             acc[r].total_iterations_fp32 += last[r].iterations_fp32;
+            acc[r].total_iterations_pair += last[r].iterations_pair;
         }
     }
     pic_status first = PIC_OK;
@@ -1272,6 +1298,7 @@ pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps, pic_step_info* inf
     for (int r = 0; r < R; ++r) {
         acc[r].iterations = last[r].iterations;
         acc[r].iterations_fp32 = last[r].iterations_fp32;
+        acc[r].iterations_pair = last[r].iterations_pair;
         acc[r].converged = last[r].converged;
         acc[r].e_v = last[r].e_v;
         acc[r].e_J = last[r].e_J;

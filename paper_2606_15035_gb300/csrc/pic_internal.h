@@ -76,6 +76,10 @@ struct StepRun {
     bool fp32 = false;                 // the next iteration runs in FP32 (PIC_MIXED)
     bool hist = false;                 // vnew holds the previous FP64 iterate v^{p-1}
     bool began32 = false;              // the step began with FP32 iterations (PIC_MIXED)
+    bool pair = false;                 // the next iteration's particle half runs in FP32 pairs
+    bool pair_issued = false;          // the iteration in flight ran in FP32 pairs
+    int ppair = 0;                     // FP32-pair iterations done in this step
+    double e_vpair_prev = INFINITY;
     int p64 = 0;                       // FP64 iterations done in this step
     bool iterating = true;             // the Picard loop is still running
     bool converged = false;
@@ -151,6 +155,7 @@ struct Ctx {
     int32_t* cell32 = nullptr;
     float *off32 = nullptr, *v32 = nullptr, *vit32 = nullptr, *vnew32 = nullptr;   // iterates: increments
     float* table32 = nullptr;            // 12 * ncell
+    float* table_pair = nullptr;         // 20 * ncell: A^n, A^{n+1}, grad phi as FP32 pairs (+ pad)
 
     // reductions and status
     double *partials = nullptr, *results = nullptr;
@@ -182,7 +187,7 @@ struct Ctx {
     double K_n = 0, W_n = 0;
 };
 
-enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_PUSH32, PH_LOCAL };
+enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_PUSH32, PH_LOCAL, PH_PUSHPAIR };
 
 // ---- launchers (particles.cu) ----
 void launch_init_positions(Ctx& c, const double* x_dev);
@@ -199,6 +204,10 @@ void launch_patch_local(Ctx& c, double* g);
 void launch_slide_out(Ctx& c, uint8_t* dst);
 void launch_permute_in(Ctx& c, const double* src_soa3, double* dst_soa3, double s0, double s1, double s2);
 void set_gauss_rule(int nq);
+
+// ---- launchers (particles_df.cu): the FP32-pair refinement push ----
+void launch_table_df(Ctx& c);
+void launch_push_df(Ctx& c, const double* vit, double* vnew, double* Jnext);
 
 // ---- launchers (particles32.cu) ----
 void launch_to32(Ctx& c);
@@ -241,6 +250,9 @@ void launch_scale_copy(Ctx& c, double* dst, const double* src, int64_t n, double
 // three-term recurrence coefficients of min(cheb_steps, cap) steps and returns that count.
 int cheb_steps(double lmin, double lmax, double eps);
 int cheb_schedule(double lmin, double lmax, double eps, double* alpha, double* beta, int cap);
+
+// Kernel parameters of the FP64 particle kernels for this context (particles.cu).
+StepParams make_params(const Ctx& c);
 
 int particle_blocks(const Ctx& c);
 int local_blocks(const Ctx& c);

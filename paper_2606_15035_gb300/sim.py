@@ -37,7 +37,7 @@ def pic_config_default(**overrides) -> PicConfig:
                 arr[a] = v[a]
         elif k == "split_orbit_at_knots" or k in ("picard_max", "quadrature", "nq", "precision", "sort_every",
                                                   "diagnostics", "accept_unconverged", "picard_accel", "mixed_max32",
-                                                  "deterministic", "shape_order", "ops"):
+                                                  "deterministic", "shape_order", "ops", "mixed_pair_max"):
             setattr(cfg, k, int(v))
         else:
             setattr(cfg, k, float(v))

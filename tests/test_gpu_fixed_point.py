@@ -127,7 +127,8 @@ def test_c1_run_is_a_fixed_point_of_algorithm1_every_step(sim, accel, precision)
     accepted iterate, which is a fixed point of the oracle's map."""
     w = pi.WORKLOADS["twostream-8c-8k"]
     x, v, q, m = pi.workload_particles(w)
-    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_accel=accel, precision=precision)
+    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_accel=accel, precision=precision,
+                   picard_max=w.picard_max)
     worst = 0.0
     for k in range(w.steps):
         o_n = oracle_level(s, q, m)
