@@ -124,8 +124,9 @@ typedef struct {
                                      next-orbit current) runs in FP32-pair arithmetic (two floats
                                      per value, a 48-bit significand, on the FP32 pipes) before the
                                      FP64 iterations; they stop early once e_v and e_J are <=
-                                     picard_tol or stop shrinking.  0: none (FP64 refinement from
-                                     the FP32 iterate).  Not used in deterministic mode */
+                                     picard_tol or stop shrinking.  0 (default): none, FP64
+                                     refinement from the FP32 iterate.  Not used in deterministic
+                                     mode */
 } pic_config;
 
 #define PIC_OPS_CENTRAL2 0
@@ -230,7 +231,8 @@ typedef struct {
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
  * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
- * at most 8 FP32 iterations, not deterministic, linear shapes (r = 1), central-difference operators. */
+ * at most 8 FP32 iterations, no FP32-pair refinement, FP64 refinement to picard_tol, not
+ * deterministic, linear shapes (r = 1), central-difference operators. */
 pic_status pic_config_default(pic_config* cfg);
 
 /* Create a context: copies the particles to the device, sorts them by cell, deposits
@@ -290,6 +292,42 @@ pic_status pic_get_accepted(pic_ctx* ctx, double* v_iter, uint8_t* slide, int32_
  * and stops; the step returns PIC_ERR_TIMEOUT and keeps the committed state.  A short bound
  * is how a caller (or a test) checks that path without a fault.  PIC_ERR_ARG for cycles < 1. */
 pic_status pic_set_wait_limit(pic_ctx* ctx, int64_t cycles);
+
+/* ---- Adjoint of the step (reverse mode) ---------------------------------------------------
+ *
+ * For a scalar L of the state after a step, the adjoint maps lambda' = dL/d(state n+1) to
+ * lambda = dL/d(state n) through Algorithm 1's implicit step: the accepted iterate v* solves
+ * v* = G(v*; state n), and the implicit-function theorem gives its adjoint mu from the
+ * transposed fixed point mu = F_v*^T (lambda' + mu on v^{n+1}), F being the final sweep
+ * (§5.4).  The per-particle derivatives of the orbit integrals (Appendices A and B, with the
+ * motion of every knot-crossing breakpoint, §4.3) come from forward-mode dual numbers through
+ * the same closed forms; the mesh half is the transposed continuity and Crank--Nicolson update
+ * (the Helmholtz operator is symmetric).  Positions' adjoints are per physical unit.  The
+ * adjoint of v^{n-1} is zero (it only sets the first Picard iterate). */
+typedef struct {
+    int32_t iterations;   /* block-Jacobi iterations of the transposed fixed point (+ the final sweep) */
+    double residual;      /* its last relative change ||mu_new - mu|| / ||mu_new|| */
+} pic_vjp_info;
+
+/* lam_prev = (d state^{n+1} / d state^n)^T lam_next for the step that the last pic_step
+ * committed (call it right after that pic_step: the context keeps level n and v* until the next
+ * step begins).  Views as in pic_state_view (NULL members of lam_next are zero; NULL members of
+ * lam_prev are not written).  Needs closed-form linear orbits and central differences;
+ * PIC_ERR_ARG if a component of the step slid onto a knot (the sliding equations are not
+ * differentiated), PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-13 in
+ * 60 iterations.  Allocates its work buffers (about 40 np + 50 ncell doubles) on first use. */
+pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_state_view* lam_prev,
+                        pic_vjp_info* info);
+
+/* lam = dW/d(state) of the current state, W the field energy (Eq. (field-energy)): nonzero for
+ * phi, A and U only (the other members, when given, are zeroed). */
+pic_status pic_energy_vjp(pic_ctx* ctx, const pic_state_view* lam);
+
+/* The adjoint of pic_init's map from the initial particles (x^0, v^0) to the initial state
+ * (§5.4: rho^0 deposited and projected, phi^0 from Poisson, P^0 = m v^0, v^{-1} = v^0):
+ * lam_x0, lam_v0 (3 * np each, pic_init order) from the state adjoint lam0.  Only valid while
+ * the context still holds pic_init's state. */
+pic_status pic_init_vjp(pic_ctx* ctx, const pic_state_view* lam0, double* lam_x0, double* lam_v0, int32_t on_device);
 
 /* Switch live profiling on (1) or off (0).  If `out` is non-NULL the accumulated profile is
  * copied there (after synchronising the stream) and the accumulators are reset. */

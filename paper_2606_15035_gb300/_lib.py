@@ -31,7 +31,7 @@ PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 PIC_OPS_CENTRAL2, PIC_OPS_SPECTRAL = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
-            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_get_accepted", "pic_set_wait_limit", "pic_profile", "pic_residual_history",
+            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_get_accepted", "pic_set_wait_limit", "pic_step_vjp", "pic_energy_vjp", "pic_init_vjp", "pic_profile", "pic_residual_history",
             "pic_cn_update_static", "pic_probe_fma_rates", "pic_last_error", "pic_destroy", "pic_autotune", "pic_ensemble_init", "pic_ensemble_step",
             "pic_ensemble_size", "pic_ensemble_run", "pic_ensemble_last_error", "pic_ensemble_destroy"]
 
@@ -137,6 +137,10 @@ class PicIterateOut(C.Structure):
     ]
 
 
+class PicVjpInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("residual", C.c_double)]
+
+
 class PicProfile(C.Structure):
     _fields_ = [
         ("launches", C.c_int64),
@@ -192,6 +196,9 @@ def lib():
     L.pic_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_accepted.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_set_wait_limit.argtypes = [C.c_void_p, C.c_int64]
+    L.pic_step_vjp.argtypes = [C.c_void_p, P(PicStateView), P(PicStateView), P(PicVjpInfo)]
+    L.pic_energy_vjp.argtypes = [C.c_void_p, P(PicStateView)]
+    L.pic_init_vjp.argtypes = [C.c_void_p, P(PicStateView), C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_cn_update_static.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_double] + [C.c_void_p] * 10 + [C.c_void_p]
     L.pic_probe_fma_rates.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]

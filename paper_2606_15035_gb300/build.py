@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpic.so")
-SOURCES = ["particles.cu", "particles32.cu", "particles_df.cu", "mesh.cu", "spectral.cu", "pic_abi.cu", "cn_static.cu", "probe.cu"]
+SOURCES = ["particles.cu", "particles32.cu", "particles_df.cu", "mesh.cu", "spectral.cu", "pic_abi.cu", "cn_static.cu", "probe.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177"]

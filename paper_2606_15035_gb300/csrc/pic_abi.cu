@@ -374,6 +374,31 @@ pic_status allocate(pic_ctx* ctx) {
     return check_cuda(ctx, "allocate");
 }
 
+// out = sigma1 (-Delta_h)^+ rhs on the non-null modes, by Chebyshev iteration from zero (rhs
+// must have no null-mode part; out is projected off them).  spare: a scratch mesh field.
+void poisson_into(Ctx& c, const double* rhs, double* out, double* spare) {
+    const int64_t N = c.m.ncell;
+    double lmax = 0.0, lmin = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        double mx, mn;
+        sin2_range(c.cfg.n[ax], mx, mn);
+        lmax += mx * c.invH[ax] * c.invH[ax];
+        if (mn > 0.0) {
+            double v = mn * c.invH[ax] * c.invH[ax];
+            lmin = lmin == 0.0 ? v : std::min(lmin, v);
+        }
+    }
+    launch_fill(c, out, N, 0.0);
+    if (!(lmin > 0.0)) return;
+    std::vector<double> al(4096), be(4096);
+    const int it = cheb_schedule(lmin / c.cfg.sigma1, lmax / c.cfg.sigma1, c.cfg.helmholtz_tol, al.data(), be.data(), 4096);
+    double* x = out;
+    double* sp = spare;
+    launch_helmholtz(c, rhs, 0.0, 1.0 / c.cfg.sigma1, 1, it, al.data(), be.data(), &x, &sp);
+    if (x != out) cudaMemcpyAsync(out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, c.stream);
+    launch_null_project(c, out, 0.0);
+}
+
 // -Delta_h phi = sigma1 rho on the non-null modes by Chebyshev iteration (rho projected).
 pic_status solve_poisson(pic_ctx* ctx) {
     Ctx& c = ctx->c;
@@ -457,6 +482,7 @@ void step_begin(Ctx& c) {
     // state was kept, so the context is usable again
     cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
     c.have_accepted = false;
+    c.fresh_init = false;
     if (np > 0 && c.cfg.sort_every > 0 && c.steps % c.cfg.sort_every == 0) {
         ProfScope ps(c, PH_SORT);
         launch_sort(c);
@@ -771,7 +797,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->picard_accel = 1;
     cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
-    cfg->mixed_pair_max = 8;
+    cfg->mixed_pair_max = 0;
     cfg->deterministic = 0;
     cfg->shape_order = 1;
     cfg->ops = PIC_OPS_CENTRAL2;
@@ -846,6 +872,7 @@ pic_status pic_init(const pic_config* cfg, const pic_particles* particles, const
         delete ctx;
         return s;
     }
+    c.fresh_init = true;
     *out = ctx;
     return PIC_OK;
 }
@@ -941,6 +968,7 @@ pic_status pic_set_state(pic_ctx* ctx, const pic_state_view* src) {
     cudaMemcpyAsync(c.rho0, src->rho, sizeof(double) * N, kind, c.stream);
     c.have_diag = false;
     c.have_accepted = false;
+    c.fresh_init = false;
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_set_state");
     return check_cuda(ctx, "pic_set_state");
 }
@@ -1040,6 +1068,234 @@ pic_status pic_get_accepted(pic_ctx* ctx, double* v_iter, uint8_t* slide, int32_
     }
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_accepted");
     return check_cuda(ctx, "pic_get_accepted");
+}
+
+// ---- adjoint --------------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+pic_status adj_alloc(pic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    if (c.adj_tab) return PIC_OK;
+    const int64_t np3 = 3 * std::max<int64_t>(c.np, 1), N = c.m.ncell;
+    ALLOC(c.adj_xe, double, np3);
+    ALLOC(c.adj_v, double, np3);
+    ALLOC(c.adj_P, double, np3);
+    ALLOC(c.adj_mu, double, np3);
+    ALLOC(c.adj_mu2, double, np3);
+    ALLOC(c.adj_xi, double, np3);
+    ALLOC(c.adj_g, double, np3);
+    ALLOC(c.adj_tmp, double, np3);
+    ALLOC(c.adj_B, double, 3 * np3);
+    ALLOC(c.adj_F1, double, 4 * N);
+    ALLOC(c.adj_W1, double, 4 * N);
+    ALLOC(c.adj_rho1, double, N);
+    ALLOC(c.adj_t, double, 4 * N);
+    ALLOC(c.adj_pn, double, 4 * N);
+    ALLOC(c.adj_y, double, 4 * N);
+    ALLOC(c.adj_ys, double, 4 * N);
+    ALLOC(c.adj_J, double, 3 * N);
+    ALLOC(c.adj_F0, double, 4 * N);
+    ALLOC(c.adj_W0, double, 4 * N);
+    ALLOC(c.adj_rho0, double, N);
+    ALLOC(c.adj_tab, double, 9 * N);
+    return check_cuda(ctx, "adjoint buffers");
+}
+
+// Particle array (3 np, caller order, host or device) -> device order, times s per component.
+void adj_in(Ctx& c, const double* src, cudaMemcpyKind kind, double* dst, const double s[3]) {
+    if (src) {
+        cudaMemcpyAsync(c.sort_tmp, src, sizeof(double) * 3 * c.np, kind, c.stream);
+        launch_permute_in(c, c.sort_tmp, dst, s[0], s[1], s[2]);
+    } else {
+        cudaMemsetAsync(dst, 0, sizeof(double) * 3 * c.np, c.stream);
+    }
+}
+
+void adj_out(Ctx& c, const double* src, double* dst, cudaMemcpyKind kind, const double s[3]) {
+    if (!dst) return;
+    launch_unpermute(c, src, c.sort_tmp, s[0], s[1], s[2]);
+    cudaMemcpyAsync(dst, c.sort_tmp, sizeof(double) * 3 * c.np, kind, c.stream);
+}
+
+void mesh_in(Ctx& c, const double* src, cudaMemcpyKind kind, double* dst, int64_t n) {
+    if (src) cudaMemcpyAsync(dst, src, sizeof(double) * n, kind, c.stream);
+    else cudaMemsetAsync(dst, 0, sizeof(double) * n, c.stream);
+}
+
+void mesh_out(Ctx& c, const double* src, double* dst, cudaMemcpyKind kind, int64_t n) {
+    if (dst) cudaMemcpyAsync(dst, src, sizeof(double) * n, kind, c.stream);
+}
+
+// One transposed sweep at (level n, v*) for the velocity-output adjoint lam_v + mu: the mesh
+// adjoints (adj_F0, adj_W0, adj_rho0, adj_J), and per particle adj_xi, adj_g, adj_B.
+void adj_sweep(Ctx& c, const double* xi_n, const double* v_n, const double* vstar) {
+    const int64_t N = c.m.ncell;
+    const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
+    cudaMemsetAsync(c.adj_tab, 0, sizeof(double) * 9 * N, c.stream);
+    launch_adj_scatter(c, xi_n, v_n, vstar, c.adj_P, c.adj_v, c.adj_mu, c.adj_tab);
+    launch_adj_mesh_rhs(c, c.adj_tab, c.adj_F1, c.adj_W1, c.adj_t, c.adj_pn);
+    cudaMemsetAsync(c.adj_y, 0, sizeof(double) * 4 * N, c.stream);
+    double* y = c.adj_y;
+    double* ys = c.adj_ys;
+    launch_helmholtz(c, c.adj_t, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, &y, &ys);
+    launch_adj_mesh_out(c, y, c.adj_pn, c.adj_W1, c.adj_rho1, c.adj_F0, c.adj_W0, c.adj_rho0, c.adj_J);
+    launch_adj_derivs(c, xi_n, v_n, vstar, c.adj_J, c.adj_P, c.adj_v, c.adj_xe, c.adj_mu, c.adj_xi, c.adj_g, c.adj_B);
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_state_view* lam_prev,
+                        pic_vjp_info* info) {
+    if (!ctx || !lam_next || !lam_prev) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    c.err.clear();
+    if (!c.have_accepted)
+        return fail(ctx, PIC_ERR_ARG, "pic_step_vjp: only available right after a committed pic_step");
+    if (c.cfg.quadrature != PIC_QUAD_CLOSED || c.cfg.shape_order != 1 || c.cfg.ops != PIC_OPS_CENTRAL2)
+        return fail(ctx, PIC_ERR_ARG, "pic_step_vjp: needs the closed-form linear orbits and central differences");
+    pic_status s = adj_alloc(ctx);
+    if (s != PIC_OK) return s;
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kin = lam_next->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = lam_prev->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const double one[3] = {1.0, 1.0, 1.0};
+    const double toc[3] = {c.H[0], c.H[1], c.H[2]};        // d/dxi = H d/dx
+    const double tox[3] = {c.invH[0], c.invH[1], c.invH[2]};
+    // level n and the accepted iterate, as the committed step left them (device order)
+    const double* xi_n = c.xi_new;
+    const double* v_n = c.vprev;
+    const double* vstar = c.vit;
+    cudaMemsetAsync(c.dev_status, 0, sizeof(int), c.stream);
+    if (np > 0) {
+        adj_in(c, lam_next->x, kin, c.adj_xe, toc);
+        adj_in(c, lam_next->v, kin, c.adj_v, one);
+        adj_in(c, lam_next->P, kin, c.adj_P, one);
+        cudaMemsetAsync(c.adj_mu, 0, sizeof(double) * 3 * np, c.stream);
+        launch_adj_slide_check(c);
+    }
+    mesh_in(c, lam_next->phi, kin, c.adj_F1, N);
+    mesh_in(c, lam_next->A, kin, c.adj_F1 + N, 3 * N);
+    mesh_in(c, lam_next->psi, kin, c.adj_W1, N);
+    mesh_in(c, lam_next->U, kin, c.adj_W1 + N, 3 * N);
+    mesh_in(c, lam_next->rho, kin, c.adj_rho1, N);
+    s = sync_results(ctx, "pic_step_vjp");
+    if (s != PIC_OK) return s;
+    if (*c.host_status & DEV_ERR_SLIDE)
+        return fail(ctx, PIC_ERR_ARG, "pic_step_vjp: a component of this step slides on a knot (not differentiated)");
+    // the transposed fixed point for mu, block-Jacobi
+    const double tol = 1e-13;
+    const int max_it = 60;
+    int it = 0;
+    double res = 0.0;
+    for (it = 0; np > 0 && it < max_it; ++it) {
+        adj_sweep(c, xi_n, v_n, vstar);
+        const int nb = launch_adj_jacobi(c, c.adj_g, c.adj_B, c.adj_mu, c.adj_mu2);
+        launch_finalize(c, S_EV_NUM, 2, nb, false);
+        s = sync_results(ctx, "pic_step_vjp");
+        if (s != PIC_OK) return s;
+        const double num = c.host_results[S_EV_NUM], den = c.host_results[S_EV_DEN];
+        res = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        std::swap(c.adj_mu, c.adj_mu2);
+        if (!std::isfinite(res)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step_vjp: non-finite adjoint");
+        if (res <= tol) break;
+    }
+    if (np > 0 && it >= max_it)
+        return fail(ctx, PIC_ERR_NO_CONVERGENCE, "pic_step_vjp: the transposed fixed point did not converge");
+    // the outputs at the converged mu
+    adj_sweep(c, xi_n, v_n, vstar);
+    if (np > 0) {
+        adj_out(c, c.adj_xi, lam_prev->x, kout, tox);
+        adj_out(c, c.adj_g, lam_prev->v, kout, one);                    // beta's v^n = its v*
+        cudaMemcpyAsync(c.adj_tmp, c.adj_v, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
+        launch_adj_axpy(c, 3 * np, c.adj_tmp, c.adj_mu, 1.0);
+        cudaMemcpyAsync(c.adj_g, c.adj_P, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
+        launch_adj_axpy(c, 3 * np, c.adj_g, c.adj_tmp, 1.0 / c.mass);   // P^{n+1} = P^n + ...: lam_P + lam_v1 / m
+        adj_out(c, c.adj_g, lam_prev->P, kout, one);
+        if (lam_prev->vprev) cudaMemsetAsync(lam_prev->vprev, 0, sizeof(double) * 3 * np, c.stream);
+    }
+    mesh_out(c, c.adj_F0, lam_prev->phi, kout, N);
+    mesh_out(c, c.adj_F0 + N, lam_prev->A, kout, 3 * N);
+    mesh_out(c, c.adj_W0, lam_prev->psi, kout, N);
+    mesh_out(c, c.adj_W0 + N, lam_prev->U, kout, 3 * N);
+    mesh_out(c, c.adj_rho0, lam_prev->rho, kout, N);
+    s = sync_results(ctx, "pic_step_vjp");
+    if (s != PIC_OK) return s;
+    if (info) {
+        info->iterations = it + 1;
+        info->residual = res;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_energy_vjp(pic_ctx* ctx, const pic_state_view* lam) {
+    if (!ctx || !lam) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.cfg.ops != PIC_OPS_CENTRAL2) return fail(ctx, PIC_ERR_ARG, "pic_energy_vjp: needs central differences");
+    pic_status s = adj_alloc(ctx);
+    if (s != PIC_OK) return s;
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kout = lam->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    launch_energy_grad(c, c.adj_F0, c.adj_W0);
+    mesh_out(c, c.adj_F0, lam->phi, kout, N);
+    mesh_out(c, c.adj_F0 + N, lam->A, kout, 3 * N);
+    mesh_out(c, c.adj_W0, lam->psi, kout, N);
+    mesh_out(c, c.adj_W0 + N, lam->U, kout, 3 * N);
+    double* zeros[5] = {lam->x, lam->v, lam->P, lam->vprev, lam->rho};
+    const int64_t counts[5] = {3 * np, 3 * np, 3 * np, 3 * np, N};
+    for (int k = 0; k < 5; ++k) {
+        if (!zeros[k] || counts[k] == 0) continue;
+        if (lam->on_device) cudaMemsetAsync(zeros[k], 0, sizeof(double) * counts[k], c.stream);
+        else std::memset(zeros[k], 0, sizeof(double) * counts[k]);
+    }
+    return sync_results(ctx, "pic_energy_vjp");
+}
+
+pic_status pic_init_vjp(pic_ctx* ctx, const pic_state_view* lam0, double* lam_x0, double* lam_v0, int32_t on_device) {
+    if (!ctx || !lam0) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    c.err.clear();
+    if (!c.fresh_init)
+        return fail(ctx, PIC_ERR_ARG, "pic_init_vjp: the state must be pic_init's (no step or set_state since)");
+    if (c.cfg.ops != PIC_OPS_CENTRAL2 || c.cfg.shape_order != 1)
+        return fail(ctx, PIC_ERR_ARG, "pic_init_vjp: needs central differences and linear shapes");
+    pic_status s = adj_alloc(ctx);
+    if (s != PIC_OK) return s;
+    const int64_t np = c.np, N = c.m.ncell;
+    const cudaMemcpyKind kin = lam0->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const double one[3] = {1.0, 1.0, 1.0};
+    const double tox[3] = {c.invH[0], c.invH[1], c.invH[2]};
+    // phi^0 = sigma1 (-Delta_h)^+ rho^0 and rho^0 = (deposit + n0) off the null modes: both
+    // maps are symmetric, so lam_dep = P (lam_rho + sigma1 (-Delta_h)^+ P lam_phi)
+    mesh_in(c, lam0->phi, kin, c.adj_t, N);
+    mesh_in(c, lam0->rho, kin, c.adj_rho1, N);
+    launch_null_project(c, c.adj_t, 0.0);
+    poisson_into(c, c.adj_t, c.adj_y, c.adj_ys);
+    launch_adj_axpy(c, N, c.adj_rho1, c.adj_y, 1.0);
+    launch_null_project(c, c.adj_rho1, 0.0);
+    if (np > 0) {
+        // positions: the direct adjoint plus the deposit's transpose (cell units, device order)
+        cudaMemsetAsync(c.adj_xi, 0, sizeof(double) * 3 * np, c.stream);
+        launch_adj_deposit(c, c.xi, c.adj_rho1, c.adj_xi);
+        adj_in(c, lam0->x, kin, c.adj_xe, one);
+        launch_unpermute(c, c.adj_xi, c.adj_tmp, tox[0], tox[1], tox[2]);   // caller order, physical
+        launch_permute_in(c, c.adj_tmp, c.adj_g, 1.0, 1.0, 1.0);           // back to device order
+        launch_adj_axpy(c, 3 * np, c.adj_xe, c.adj_g, 1.0);
+        adj_out(c, c.adj_xe, lam_x0, kout, one);
+        // velocities: v^0 sets v, v^{-1} = v^0 and P^0 = m v^0 (A^0 = 0)
+        adj_in(c, lam0->v, kin, c.adj_v, one);
+        adj_in(c, lam0->vprev, kin, c.adj_g, one);
+        launch_adj_axpy(c, 3 * np, c.adj_v, c.adj_g, 1.0);
+        adj_in(c, lam0->P, kin, c.adj_g, one);
+        launch_adj_axpy(c, 3 * np, c.adj_v, c.adj_g, c.mass);
+        adj_out(c, c.adj_v, lam_v0, kout, one);
+    }
+    return sync_results(ctx, "pic_init_vjp");
 }
 
 pic_status pic_set_wait_limit(pic_ctx* ctx, int64_t cycles) {

@@ -172,6 +172,17 @@ struct Ctx {
     double cheb_rate = 0.0;            // 1 / log(1 / rho) of the Chebyshev bound (0: one step)
     double* cheb_red = nullptr;        // per-block sums of the cooperative solve (8 per block)
 
+    // adjoint (pic_step_vjp / pic_init_vjp), allocated on first use: particles (3 np each) the
+    // adjoints of x^{n+1} (cell units), v^{n+1}, P^{n+1}, of v* (two buffers), of x^n, the
+    // block-Jacobi right-hand side g and blocks B (9 np), a scratch; mesh: the gather table's
+    // adjoint (9 N), the level-(n+1) inputs and level-n outputs, the Helmholtz buffers, J's adjoint
+    bool fresh_init = false;             // the state is pic_init's (no step or set_state since)
+    double *adj_xe = nullptr, *adj_v = nullptr, *adj_P = nullptr, *adj_mu = nullptr, *adj_mu2 = nullptr;
+    double *adj_xi = nullptr, *adj_g = nullptr, *adj_B = nullptr, *adj_tmp = nullptr;
+    double *adj_tab = nullptr, *adj_F1 = nullptr, *adj_W1 = nullptr, *adj_rho1 = nullptr;
+    double *adj_t = nullptr, *adj_pn = nullptr, *adj_y = nullptr, *adj_ys = nullptr, *adj_J = nullptr;
+    double *adj_F0 = nullptr, *adj_W0 = nullptr, *adj_rho0 = nullptr;
+
     // live profiling: event pairs per phase, resolved at the next stream synchronisation
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -208,6 +219,21 @@ void set_gauss_rule(int nq);
 // ---- launchers (particles_df.cu): the FP32-pair refinement push ----
 void launch_table_df(Ctx& c);
 void launch_push_df(Ctx& c, const double* vit, double* vnew, double* Jnext);
+
+// ---- launchers (adjoint.cu) ----
+void launch_adj_scatter(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lam_P,
+                        const double* lam_v, const double* mu, double* lam_tab);
+void launch_adj_mesh_rhs(Ctx& c, const double* lam_tab, const double* lF1, const double* lW1, double* t, double* pn);
+void launch_adj_mesh_out(Ctx& c, const double* y, const double* pn, const double* lW1, const double* lrho1,
+                         double* lF0, double* lW0, double* lrho0, double* lJ);
+void launch_adj_derivs(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lJ,
+                       const double* lam_P, const double* lam_v, const double* lam_xe, const double* mu,
+                       double* lam_xi, double* g, double* B);
+int launch_adj_jacobi(Ctx& c, const double* g, const double* B, const double* mu, double* mu_new);
+void launch_adj_axpy(Ctx& c, int64_t n, double* y, const double* x, double s);
+void launch_adj_slide_check(Ctx& c);
+void launch_adj_deposit(Ctx& c, const double* xi, const double* lam_dep, double* lam_xi);
+void launch_energy_grad(Ctx& c, double* lF, double* lW);
 
 // ---- launchers (particles32.cu) ----
 void launch_to32(Ctx& c);

@@ -17,7 +17,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PIC_FP64, PIC_QUAD_CLOSED, PIC_QUAD_GAUSS, PicAllocator, PicConfig, PicDiag,  # noqa: F401
-                   PicEnergy, PicError, PicIterateOut, PicParticles, PicProfile, PicStateView, PicStepInfo)
+                   PicEnergy, PicError, PicIterateOut, PicParticles, PicProfile, PicStateView, PicStepInfo,
+                   PicVjpInfo)
 
 
 def _check(status, ctx=None):
@@ -320,6 +321,53 @@ class PicSim:
         pt = {k: b.reshape(3, npart).T.copy() for k, b in bufs.items()}
         return HostState(**pt, **{k: _mesh_to_xyz(v, self.n) for k, v in mesh.items()},
                          **{k: _mesh_to_xyz(v, self.n) for k, v in vec.items()})
+
+    # ---- device-resident state and the adjoint (flat arrays in the library's layouts) ----
+
+    STATE_KEYS = ("x", "v", "P", "vprev", "phi", "psi", "rho", "A", "U")
+
+    def state_zeros(self):
+        """A dict of zero float64 CUDA tensors in the state layout: particles SoA (3 np),
+        mesh x-fastest (ncell, or 3 ncell for A and U)."""
+        torch = _torch()
+        sizes = {"x": 3 * self.np, "v": 3 * self.np, "P": 3 * self.np, "vprev": 3 * self.np, "phi": self.ncell,
+                 "psi": self.ncell, "rho": self.ncell, "A": 3 * self.ncell, "U": 3 * self.ncell}
+        return {k: torch.zeros(max(n, 1), dtype=torch.float64, device="cuda") for k, n in sizes.items()}
+
+    def _dview(self, d):
+        return PicStateView(*[d[k].data_ptr() for k in self.STATE_KEYS], 1)
+
+    def get_state_device(self):
+        d = self.state_zeros()
+        pic_get_state(self.ctx, self._dview(d))
+        return d
+
+    def set_state_device(self, d):
+        pic_set_state(self.ctx, self._dview(d))
+
+    def step_vjp(self, lam_next):
+        """(d state^{n+1} / d state^n)^T lam_next for the step just committed: (lam_prev, info)."""
+        lam_prev = self.state_zeros()
+        info = PicVjpInfo()
+        _check(_lib.lib().pic_step_vjp(self.ctx, C.byref(self._dview(lam_next)), C.byref(self._dview(lam_prev)),
+                                       C.byref(info)), self.ctx)
+        return lam_prev, info
+
+    def energy_vjp(self):
+        """dW/d(state) of the current state, W the field energy."""
+        lam = self.state_zeros()
+        _check(_lib.lib().pic_energy_vjp(self.ctx, C.byref(self._dview(lam))), self.ctx)
+        return lam
+
+    def init_vjp(self, lam0):
+        """(lam_x0, lam_v0), each 3 np SoA: the adjoint of pic_init's map from the initial
+        particles to the initial state (the context must still hold pic_init's state)."""
+        torch = _torch()
+        lx = torch.zeros(max(3 * self.np, 1), dtype=torch.float64, device="cuda")
+        lv = torch.zeros_like(lx)
+        _check(_lib.lib().pic_init_vjp(self.ctx, C.byref(self._dview(lam0)), lx.data_ptr(), lv.data_ptr(), 1),
+               self.ctx)
+        return lx, lv
 
     def set_state(self, s: HostState):
         arrs = [soa(s.x), soa(s.v), soa(s.P), soa(s.vprev),

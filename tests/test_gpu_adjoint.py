@@ -1,0 +1,163 @@
+"""The hand-written adjoint of the implicit step (pic_step_vjp, pic_energy_vjp, pic_init_vjp) and
+the differentiable run built on it (paper_2606_15035_gb300.adjoint, a torch.autograd.Function
+with checkpoint-and-recompute over time steps).
+
+Checks, from the smallest to the configured run:
+
+* one step: <lambda', (S(s + h d) - S(s - h d)) / 2h> against <VJP(lambda'), d> for random
+  directions d in every state component and random lambda', S being one GPU step (central
+  differences of the library's own forward step);
+* the field energy after a few steps at 8^3, d W^N / d eps (perturbation amplitude) and
+  d W^N / d v0 (beam speed), against the FP64 oracle's reference derivative (a Richardson-
+  extrapolated central difference of the oracle's own steps, oracle/derivatives.py);
+* the configured adjoint run: 32^3, 16 particles per cell (524,288 electrons), 100 steps with
+  a checkpoint every 10, d W^N / d eps, d W^N / d v0 and a directional derivative along
+  the initial canonical momenta P^0, against central differences with h = 1e-6 of the GPU run.
+
+The step map is only C0 where an orbit endpoint crosses a knot (the D_i A integrand and the
+point interpolant have kinks there, §4.3): a difference quotient whose interval holds such an
+event measures an average slope, not the derivative.  Over 100 steps of 524k particles some
+events fall inside the h = 1e-6 interval, which is what limits the agreement of the last check.
+"""
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim(cuda_ok):
+    from paper_2606_15035_gb300 import build
+    build.build()
+    from paper_2606_15035_gb300 import sim as s
+    return s
+
+
+def _dot(a, b, keys):
+    return sum(float((a[k] * b[k]).sum()) for k in keys)
+
+
+def test_one_step_vjp_matches_directional_differences(sim):
+    import torch
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.random_twostream(w.n, w.L, 2, 0.2, 1e-2, 1e-3, 7301)
+    cfg = sim.pic_config_default(n=w.n, L=w.L, dt=0.1, picard_tol=1e-14, picard_max=32)
+    s = sim.PicSim(cfg, x, v, q, m)
+    s.step(3)                                          # fields and psi, A, U non-zero
+    base = s.get_state_device()
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    scale = {"x": 1e-3, "v": 1e-3, "P": 1e-3 * m, "vprev": 0.0, "phi": 1e-3, "psi": 1e-3, "rho": 1e-3, "A": 1e-3,
+             "U": 1e-3}
+    d = {k: scale[k] * torch.randn(t.shape, generator=gen, device="cuda", dtype=torch.float64) for k, t in base.items()}
+    lam = {k: torch.randn(t.shape, generator=gen, device="cuda", dtype=torch.float64) for k, t in base.items()}
+    lam["vprev"].zero_()
+    keys = ("x", "v", "P", "phi", "psi", "rho", "A", "U")
+    Lv = torch.tensor(w.L, dtype=torch.float64, device="cuda")
+
+    def step_from(st):
+        s.set_state_device(st)
+        assert s.step(1).converged
+        return s.get_state_device()
+
+    h = 1e-4
+    plus = step_from({k: base[k] + h * d[k] for k in base})
+    minus = step_from({k: base[k] - h * d[k] for k in base})
+    diff = {k: plus[k] - minus[k] for k in base}
+    dx = diff["x"].reshape(3, -1)
+    diff["x"] = (((dx + 0.5 * Lv[:, None]) % Lv[:, None]) - 0.5 * Lv[:, None]).reshape(-1)   # minimal image
+    fd = _dot(lam, diff, keys) / (2 * h)
+    s.set_state_device(base)
+    assert s.step(1).converged
+    lam_prev, info = s.step_vjp(lam)
+    adj = _dot(lam_prev, d, keys)
+    assert info.iterations < 60 and info.residual <= 1e-13
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd, info.iterations)
+    s.close()
+
+
+def _family(n, L, ppb, v0, eps, seed):
+    """Uniform start positions and the beams' signs, for x0(eps) = xu + eps sin(k1 xu) e_x and
+    v0 = +-v0 e_x, exactly as pic_inputs.random_twostream builds them."""
+    xu, vv, q, m = pi.random_twostream(n, L, ppb, v0, 0.0, 0.0, seed)
+    sign = np.sign(vv[:, 0])
+    return xu, sign, q, m
+
+
+def _initial(torch, xu, sign, m, L, eps, v0):
+    k1 = 2 * np.pi / L[0]
+    X = torch.as_tensor(xu, device="cuda")
+    S = torch.as_tensor(sign, device="cuda")
+    ex = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ex[0] = 1.0
+    x0 = X + eps * torch.sin(k1 * X[:, :1]) * ex
+    P0 = m * v0 * S[:, None] * ex
+    return x0, P0
+
+
+@pytest.mark.parametrize("param", ["eps", "v0"])
+def test_field_energy_gradient_matches_the_oracle_at_8c(sim, param):
+    import torch
+    from oracle import derivatives as dv
+    from oracle import pic as opic
+    from paper_2606_15035_gb300 import adjoint
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    n, L, ppb, seed, nsteps = w.n, w.L, 2, 7401, 4
+    v0, eps = 0.2, 1e-3
+    xu, sign, q, m = _family(n, L, ppb, v0, eps, seed)
+    cfg = sim.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-14, picard_max=32)
+    e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
+    x0, P0 = _initial(torch, xu, sign, m, L, e, b)
+    W = adjoint.field_energy_after(x0, P0, cfg, q, m, nsteps, every=2)
+    W.backward()
+    got = float(e.grad if param == "eps" else b.grad)
+    ocfg = opic.Config(n=n, L=L, dt=0.1, picard_tol=1e-14, picard_max=32)
+    if param == "eps":
+        ref = dv.directional_derivative(lambda s: pi.random_twostream(n, L, ppb, v0, eps + s, 0.0, seed), ocfg,
+                                        nsteps, 1e-2 * eps)
+    else:
+        ref = dv.directional_derivative(lambda s: pi.random_twostream(n, L, ppb, v0 + s, eps, 0.0, seed), ocfg,
+                                        nsteps, 1e-4)
+    assert abs(got - ref) <= 1e-6 * abs(ref), (param, got, ref)
+
+
+def test_configured_adjoint_run_32c_100_steps(sim):
+    """32^3, 16 per cell (cold beams +-0.2, eps = 1e-3), 100 steps, checkpoints every 10:
+    d W^N / d eps, d W^N / d v0 and d W^N / dP^0 along a random direction u, against central
+    differences h = 1e-6 of the GPU forward run."""
+    import torch
+    from paper_2606_15035_gb300 import adjoint
+    n, L, ppb, seed, nsteps = (32, 32, 32), pi.WORKLOADS["twostream-32c-2M"].L, 8, 1400, 100
+    v0, eps = 0.2, 1e-3
+    xu, sign, q, m = _family(n, L, ppb, v0, eps, seed)
+    assert xu.shape[0] == 524288
+    cfg = sim.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-13, picard_max=32)
+    e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
+    x0, P0 = _initial(torch, xu, sign, m, L, e, b)
+    P0.retain_grad()
+    W = adjoint.field_energy_after(x0, P0, cfg, q, m, nsteps, every=10)
+    W.backward()
+    u = torch.randn(P0.shape, generator=torch.Generator(device="cuda").manual_seed(11), device="cuda",
+                    dtype=torch.float64) * m * 1e-2
+    got = {"eps": float(e.grad), "v0": float(b.grad), "P0.u": float((P0.grad * u).sum())}
+
+    def W_of(eps_, v0_, dP=0.0):
+        with torch.no_grad():
+            xa, Pa = _initial(torch, xu, sign, m, L, eps_, v0_)
+            s = sim.PicSim(cfg, xa, (Pa + dP * u) / m, q, m)
+            for _ in range(nsteps):
+                assert s.step(1).converged
+            Wn = s.energy().W
+            s.close()
+            return Wn
+
+    h = 1e-6
+    fd = {"eps": (W_of(eps + h, v0) - W_of(eps - h, v0)) / (2 * h),
+          "v0": (W_of(eps, v0 + h) - W_of(eps, v0 - h)) / (2 * h),
+          "P0.u": (W_of(eps, v0, h) - W_of(eps, v0, -h)) / (2 * h)}
+    for k in got:
+        assert abs(got[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, got[k], fd[k])

@@ -10,7 +10,9 @@ checked from the library's own profile counters, so the test runs the code paths
 134M-particle run.
 
 Targets of the mixed path: state within 1e-5 of the FP64 path in relative L2 (positions: the
-L2 norm of the minimal-image displacement over that of the positions), relative energy drift
+L2 norm of the minimal-image displacement over that of the positions; the charge density
+against the electron density's own scale n0 sqrt(N_cells), because the stored rho is the
+small fluctuation left once the uniform ion background is removed), relative energy drift
 max_n |E^n - E^0| / E^0 <= 1e-9; FP64 path drift <= 1e-12.  The map of Algorithm 1 is only C0
 where an orbit endpoint crosses a knot, so a particle whose step lands within the paths'
 rounding difference of such a crossing may take a different (equally valid) root on the two
@@ -65,9 +67,16 @@ def test_mixed_path_tracks_fp64_path_on_the_128_mesh(sim, mixed_tol64):
             d = sb.x - sa.x
             d = (d + 0.5 * Lv) % Lv - 0.5 * Lv
             assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(sa.x), (k, np.linalg.norm(d) / np.linalg.norm(sa.x))
-            for name in ("v", "P", "phi", "A", "psi", "U", "rho"):
+            for name in ("v", "P", "phi", "A", "psi", "U"):
                 err = rel(getattr(sb, name), getattr(sa, name))
                 assert err <= 1e-5, (k, name, err)
+            n0 = 1.0
+            err = np.linalg.norm(sb.rho - sa.rho) / max(np.linalg.norm(sa.rho), n0 * np.sqrt(sa.rho.size))
+            assert err <= 1e-5, (k, "rho", err)
+            # the paths agree to the solve's tolerance except for the rare particles whose step
+            # lands on a different (equally valid) root a hair from a knot crossing
+            far = np.abs(d).max(axis=1) > 1e-9 * Lv.max()
+            assert far.mean() <= 1e-5, (k, int(far.sum()))
             del sa, sb
     pa, pb = a.profile(False), b.profile(False)
     assert pa.push_pieces / pa.particle_pushes > 2.0                 # > 2 orbit pieces on average
