@@ -52,6 +52,81 @@ __device__ __forceinline__ double lap(const double* __restrict__ f, const Nb& b,
     return s;
 }
 
+// Position of a linear index over nfields stacked meshes in mixed radix (ix, iy, iz, field),
+// advanced by a fixed grid stride with carries instead of divisions: the stencil kernels below
+// would otherwise spend most of their instructions on 64-bit divisions and index wraps.
+struct MeshPos {
+    int ix, iy, iz, f;
+    int64_t g;   // node index within its field
+};
+
+struct StrideDigits {
+    int sx, sy, sz, sf;   // S = sx + n0 (sy + n1 (sz + n2 sf)), each digit below its radix
+};
+
+StrideDigits stride_digits(int64_t S, const MeshDims& m) {
+    StrideDigits d;
+    d.sx = (int)(S % m.n[0]);
+    S /= m.n[0];
+    d.sy = (int)(S % m.n[1]);
+    S /= m.n[1];
+    d.sz = (int)(S % m.n[2]);
+    d.sf = (int)(S / m.n[2]);
+    return d;
+}
+
+__device__ __forceinline__ MeshPos pos_of(int64_t idx, const MeshDims& m) {
+    MeshPos q;
+    q.ix = (int)(idx % m.n[0]);
+    int64_t t = idx / m.n[0];
+    q.iy = (int)(t % m.n[1]);
+    t /= m.n[1];
+    q.iz = (int)(t % m.n[2]);
+    q.f = (int)(t / m.n[2]);
+    q.g = (int64_t)q.ix + (int64_t)m.n[0] * ((int64_t)q.iy + (int64_t)m.n[1] * q.iz);
+    return q;
+}
+
+__device__ __forceinline__ void advance(MeshPos& q, const StrideDigits& s, const MeshDims& m) {
+    int c = 0;
+    int ix = q.ix + s.sx;
+    if (ix >= m.n[0]) ix -= m.n[0], c = 1;
+    int iy = q.iy + s.sy + c;
+    c = 0;
+    if (iy >= m.n[1]) iy -= m.n[1], c = 1;
+    int iz = q.iz + s.sz + c;
+    c = 0;
+    if (iz >= m.n[2]) iz -= m.n[2], c = 1;
+    q.f += s.sf + c;
+    q.ix = ix;
+    q.iy = iy;
+    q.iz = iz;
+    q.g = (int64_t)ix + (int64_t)m.n[0] * ((int64_t)iy + (int64_t)m.n[1] * iz);
+}
+
+// i + k wrapped onto [0, n) for |k| <= 2 (two conditional steps also cover n = 1)
+__device__ __forceinline__ int wrap2(int i, int n) {
+    if (i >= n) i -= n;
+    if (i >= n) i -= n;
+    if (i < 0) i += n;
+    if (i < 0) i += n;
+    return i;
+}
+
+// Delta_h f at q: the same sums in the same order as lap(), with wrapped offsets.
+__device__ __forceinline__ double lap_at(const double* __restrict__ f, const MeshPos& q, const MeshDims& m,
+                                         const double* invH) {
+    const int64_t g = q.g, sy = m.n[0], sz = (int64_t)m.n[0] * m.n[1];
+    const int64_t xp = g + (wrap2(q.ix + 2, m.n[0]) - q.ix), xm = g + (wrap2(q.ix - 2, m.n[0]) - q.ix);
+    const int64_t yp = g + sy * (wrap2(q.iy + 2, m.n[1]) - q.iy), ym = g + sy * (wrap2(q.iy - 2, m.n[1]) - q.iy);
+    const int64_t zp = g + sz * (wrap2(q.iz + 2, m.n[2]) - q.iz), zm = g + sz * (wrap2(q.iz - 2, m.n[2]) - q.iz);
+    const double c = f[g];
+    double s = 0.25 * invH[0] * invH[0] * (f[xp] - 2.0 * c + f[xm]);
+    s += 0.25 * invH[1] * invH[1] * (f[yp] - 2.0 * c + f[ym]);
+    s += 0.25 * invH[2] * invH[2] * (f[zp] - 2.0 * c + f[zm]);
+    return s;
+}
+
 struct MeshParams {
     MeshDims m;
     double invH[3];
@@ -147,13 +222,15 @@ __global__ void k_jdiff(int64_t n3, const double* __restrict__ Jnew, const doubl
 // d = alpha d + beta r,  x_out = x + d   (the three-term recurrence in its
 // "true residual" form, so rounding errors do not accumulate in r).
 __global__ void k_cheb(MeshParams p, const double* __restrict__ x, double* __restrict__ xout, double* __restrict__ d,
-                       const double* __restrict__ bvec, double c_id, double c_lap, double alpha, double beta) {
+                       const double* __restrict__ bvec, double c_id, double c_lap, double alpha, double beta,
+                       StrideDigits sd) {
     const int64_t N = p.m.ncell;
     const int64_t off = blockIdx.y * N;
     const double* xf = x + off;
-    GRID_LOOP(g, N) {
-        Nb b = decompose(g, p.m);
-        double Hx = c_id * xf[g] - c_lap * lap(xf, b, p.m, p.invH);
+    const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    MeshPos q = pos_of(start, p.m);
+    for (int64_t g = start; g < N; g += (int64_t)gridDim.x * blockDim.x, advance(q, sd, p.m)) {
+        double Hx = c_id * xf[g] - c_lap * lap_at(xf, q, p.m, p.invH);
         double r = bvec[off + g] - Hx;
         double dn = (alpha == 0.0 ? 0.0 : alpha * d[off + g]) + beta * r;
         d[off + g] = dn;
@@ -179,7 +256,7 @@ __global__ void __launch_bounds__(THREADS) k_cheb_all(MeshParams p, double* xa, 
                                                       const double* __restrict__ bvec, double c_id, double c_lap,
                                                       int nfields, int iters, const double* __restrict__ alpha,
                                                       const double* __restrict__ beta, double* __restrict__ red,
-                                                      double lmax, double rate, double tol) {
+                                                      double lmax, double rate, double tol, StrideDigits sd) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     __shared__ double sm[32];
     __shared__ int sK;
@@ -190,12 +267,13 @@ __global__ void __launch_bounds__(THREADS) k_cheb_all(MeshParams p, double* xa, 
         const double* x = (k & 1) ? xb : xa;
         double* xo = (k & 1) ? xa : xb;
         const double al = alpha[k], be = beta[k];
-        for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-             idx += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t f = idx / N, g = idx - f * N, off = f * N;
+        const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        MeshPos q = pos_of(start, p.m);
+        for (int64_t idx = start; idx < total; idx += (int64_t)gridDim.x * blockDim.x, advance(q, sd, p.m)) {
+            const int f = q.f;
+            const int64_t g = q.g, off = (int64_t)f * N;
             const double* xf = x + off;
-            Nb b = decompose(g, p.m);
-            double Hx = c_id * xf[g] - c_lap * lap(xf, b, p.m, p.invH);
+            double Hx = c_id * xf[g] - c_lap * lap_at(xf, q, p.m, p.invH);
             const double bv = bvec[off + g];
             double r = bv - Hx;
             if (k == 0) {
@@ -435,8 +513,9 @@ void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nf
                       const double* beta, double** x_io, double** x_spare) {
     MeshParams p = mesh_params(c);
     dim3 grid(mesh_blocks(c), nfields);
+    const StrideDigits sd = stride_digits((int64_t)grid.x * THREADS, c.m);
     for (int k = 0; k < iters; ++k) {
-        k_cheb<<<grid, THREADS, 0, c.stream>>>(p, *x_io, *x_spare, c.cheb_d, b, c_id, c_lap, alpha[k], beta[k]);
+        k_cheb<<<grid, THREADS, 0, c.stream>>>(p, *x_io, *x_spare, c.cheb_d, b, c_id, c_lap, alpha[k], beta[k], sd);
         ++c.launches;
         std::swap(*x_io, *x_spare);
     }
@@ -459,10 +538,11 @@ void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare) {
     const double* al = c.cheb_coef_dev;
     const double* be = c.cheb_coef_dev + 1024;
     double lmax = c.cheb_lmax, rate = c.cheb_rate, tol = c.cfg.helmholtz_tol;
-    void* args[] = {&p, &xa, &xb, &c.cheb_d, &bvec, &c_id, &c_lap, &nf, &iters, &al, &be, &c.cheb_red, &lmax, &rate,
-                    &tol};
     const int64_t want = (4 * c.m.ncell + THREADS - 1) / THREADS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, c.cheb_coop_blocks));
+    StrideDigits sd = stride_digits((int64_t)grid * THREADS, c.m);
+    void* args[] = {&p, &xa, &xb, &c.cheb_d, &bvec, &c_id, &c_lap, &nf, &iters, &al, &be, &c.cheb_red, &lmax, &rate,
+                    &tol, &sd};
     cudaLaunchCooperativeKernel((const void*)k_cheb_all, dim3(grid), dim3(THREADS), args, 0, c.stream);
     ++c.launches;
     if (iters & 1) std::swap(*x_io, *x_spare);
