@@ -312,10 +312,11 @@ typedef struct {
 /* lam_prev = (d state^{n+1} / d state^n)^T lam_next for the step that the last pic_step
  * committed (call it right after that pic_step: the context keeps level n and v* until the next
  * step begins).  Views as in pic_state_view (NULL members of lam_next are zero; NULL members of
- * lam_prev are not written).  Needs closed-form linear orbits and central differences;
- * PIC_ERR_ARG if a component of the step slid onto a knot (the sliding equations are not
- * differentiated), PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-13 in
- * 60 iterations.  Allocates its work buffers (about 40 np + 50 ncell doubles) on first use. */
+ * lam_prev are not written).  Needs closed-form linear orbits and central differences.  A
+ * component that slid onto a knot in that step is differentiated through the sliding
+ * equations (its iterate is the landing velocity 2 d H / dt - v^n, its momentum m v + q A_h).
+ * PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-13 in 60 iterations.
+ * Allocates its work buffers (about 45 np + 50 ncell doubles) on first use. */
 pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_state_view* lam_prev,
                         pic_vjp_info* info);
 

@@ -26,6 +26,15 @@
 //     mu_new = (I - B^T)^{-1} (g(mu) - B^T mu),
 // g(mu) being step 3's adjoint of v*.  That is the transposed counterpart of the forward
 // solve's particle-local solves: the remaining coupling is the weak one through the fields.
+//
+// Sliding components (the step committed them by the sliding equations, §9 of the notes on the
+// local solve): their iterate is the explicit landing velocity v*_a = 2 d_a H_a / dt - v^n_a,
+// d_a the start's signed distance to its knot, their velocity output is v*_a itself and their
+// momentum m v*_a + q A_h,a(x^{n+1}).  So they have no fixed-point equation (mu_a = 0, their
+// rows and columns of B are dropped), their push impulse is unused (the adjoint of P^n_a is
+// zero), the adjoint of their momentum reaches A_h at the end point and m v*_a, and the total
+// adjoint nu_a of v*_a (direct, plus the orbit's g_a) goes to the start through d_a
+// (d v*_a / d xi_a = -2 H_a / dt) and to v^n_a (-1).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -167,24 +176,40 @@ __device__ __forceinline__ void point_A1_t(const StepParams& p, const T xq[3], c
 // ---- step 1: the particles' value pass (mesh adjoints of the gather table) ---------------------
 
 // lam_tab per node: [A^n (3) | A^{n+1} (3) | grad phi^{n+1/2} (3)], 9 doubles, accumulated.
+// The output adjoints of one particle component: lP1 (of P^{n+1}), lAe (of A_h^{n+1} at the end
+// point), lg and lF (of the orbit gathers grad phi-bar and (D A)^T vbar).
+__device__ __forceinline__ void out_adjoints(const StepParams& p, bool sl, double lv, double lP, double mu_c,
+                                             double& lP1, double& lAe, double& lg, double& lF) {
+    if (sl) {             // v1 = v*, P1 = m v* + q A_end: no impulse
+        lP1 = lP;
+        lAe = p.q * lP;
+        lg = lF = 0.0;
+    } else {              // v1 = (P1 - q A_end) / m, P1 = P + dt q (-gphibar + F)
+        const double lv1 = lv + mu_c;
+        lP1 = lP + lv1 * p.inv_mass;
+        lAe = -p.q * p.inv_mass * lv1;
+        lg = -p.dt * p.q * lP1;
+        lF = p.dt * p.q * lP1;
+    }
+}
+
 __global__ void k_adj_scatter(AdjParams ap, const double* __restrict__ xi, const double* __restrict__ v,
                               const double* __restrict__ vstar, const double* __restrict__ table,
                               const double* __restrict__ lam_P, const double* __restrict__ lam_v,
-                              const double* __restrict__ mu, double* __restrict__ lam_tab) {
+                              const double* __restrict__ mu, const uint8_t* __restrict__ slide,
+                              double* __restrict__ lam_tab) {
     const StepParams& p = ap.p;
     const int64_t np = p.np;
     ADJ_LOOP(i, np) {
         double x0[3], beta[3], vb[3], lP1[3], lAe[3], lg[3], lF[3];
+        const uint8_t sb = slide[i];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             x0[a] = xi[a * np + i];
             vb[a] = 0.5 * (vstar[a * np + i] + v[a * np + i]);
             beta[a] = p.dt * vb[a] * p.invH[a];
-            const double lv1 = lam_v[a * np + i] + mu[a * np + i];
-            lP1[a] = lam_P[a * np + i] + lv1 * p.inv_mass;        // v1 = (P1 - q A_end) / m
-            lAe[a] = -p.q * p.inv_mass * lv1;
-            lg[a] = -p.dt * p.q * lP1[a];                        // P1 = P + dt q (-gphibar + F)
-            lF[a] = p.dt * p.q * lP1[a];
+            out_adjoints(p, (sb >> a) & 1u, lam_v[a * np + i], lam_P[a * np + i], mu[a * np + i], lP1[a], lAe[a], lg[a],
+                         lF[a]);
         }
         // the end point's interpolant of A^{n+1}, transposed
         double xe[3];
@@ -352,21 +377,21 @@ __global__ void __launch_bounds__(THREADS) k_adj_derivs(AdjParams ap, const doub
                                                         const double* __restrict__ table, const double* __restrict__ lJ,
                                                         const double* __restrict__ lam_P, const double* __restrict__ lam_v,
                                                         const double* __restrict__ lam_xe, const double* __restrict__ mu,
-                                                        double* __restrict__ lam_xi, double* __restrict__ gout,
-                                                        double* __restrict__ Bout, int* __restrict__ status) {
+                                                        const uint8_t* __restrict__ slide, double* __restrict__ lam_xi,
+                                                        double* __restrict__ gout, double* __restrict__ lvn,
+                                                        double* __restrict__ lPn, double* __restrict__ Bout,
+                                                        int* __restrict__ status) {
     const StepParams& p = ap.p;
     const int64_t np = p.np;
     ADJ_LOOP(i, np) {
-        double x0[3], beta[3], lg[3], lF[3], lAe[3], lxe[3];
+        double x0[3], beta[3], lg[3], lF[3], lAe[3], lxe[3], lP1[3];
+        const uint8_t sb = slide[i];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             x0[a] = xi[a * np + i];
             beta[a] = p.dt * 0.5 * (vstar[a * np + i] + v[a * np + i]) * p.invH[a];
-            const double lv1 = lam_v[a * np + i] + mu[a * np + i];
-            const double lP1 = lam_P[a * np + i] + lv1 * p.inv_mass;
-            lAe[a] = -p.q * p.inv_mass * lv1;
-            lg[a] = -p.dt * p.q * lP1;
-            lF[a] = p.dt * p.q * lP1;
+            out_adjoints(p, (sb >> a) & 1u, lam_v[a * np + i], lam_P[a * np + i], mu[a * np + i], lP1[a], lAe[a], lg[a],
+                         lF[a]);
             lxe[a] = lam_xe[a * np + i];
         }
         double dB[3][3];
@@ -396,9 +421,27 @@ __global__ void __launch_bounds__(THREADS) k_adj_derivs(AdjParams ap, const doub
         }
         if (!ok) atomicOr(status, DEV_ERR_NONFINITE);
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
+            const bool sl = (sb >> a) & 1u;
+            const double g = gout[a * np + i];          // the orbit's adjoint of v*_a (also of v^n_a)
+            if (sl) {
+                // nu_a: the direct adjoint of v*_a (its velocity and momentum outputs) plus the
+                // orbit's; v*_a = 2 d_a H_a / dt - v^n_a with d_a = knot - xi_a
+                const double nu = lam_v[a * np + i] + p.mass * lam_P[a * np + i] + g;
+                lam_xi[a * np + i] -= nu * 2.0 * p.H[a] / p.dt;
+                lvn[a * np + i] = g - nu;
+                lPn[a * np + i] = 0.0;
+                gout[a * np + i] = 0.0;                  // no fixed-point equation: mu_a = 0
+            } else {
+                lvn[a * np + i] = g;
+                lPn[a * np + i] = lP1[a];
+            }
 #pragma unroll
-            for (int d = 0; d < 3; ++d) Bout[(3 * a + d) * np + i] = dB[a][d];
+            for (int d = 0; d < 3; ++d) {
+                const bool drop = sl || ((sb >> d) & 1u);
+                Bout[(3 * a + d) * np + i] = drop ? 0.0 : dB[a][d];
+            }
+        }
     }
 }
 
@@ -459,10 +502,6 @@ __global__ void k_adj_jacobi(int64_t np, const double* __restrict__ g, const dou
 // Elementwise helpers.
 __global__ void k_adj_axpy(int64_t n, double* __restrict__ y, const double* __restrict__ x, double s) {
     ADJ_LOOP(i, n) y[i] += s * x[i];
-}
-
-__global__ void k_adj_slide_count(int64_t np, const uint8_t* __restrict__ slide, int* __restrict__ status) {
-    ADJ_LOOP(i, np) if (slide[i] & 7u) atomicOr(status, DEV_ERR_SLIDE);
 }
 
 // ---- the initial data: rho^0 = sum q S(x)/dV, phi^0 from Poisson, P^0 = m v^0 ------------------
@@ -558,7 +597,7 @@ int adj_blocks(const Ctx& c, int64_t n) {
 void launch_adj_scatter(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lam_P,
                         const double* lam_v, const double* mu, double* lam_tab) {
     k_adj_scatter<<<adj_blocks(c, c.np), THREADS, 0, c.stream>>>(adj_params(c), xi, v, vstar, c.table, lam_P, lam_v,
-                                                                  mu, lam_tab);
+                                                                  mu, c.slide, lam_tab);
     ++c.launches;
 }
 
@@ -576,9 +615,10 @@ void launch_adj_mesh_out(Ctx& c, const double* y, const double* pn, const double
 
 void launch_adj_derivs(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lJ,
                        const double* lam_P, const double* lam_v, const double* lam_xe, const double* mu,
-                       double* lam_xi, double* g, double* B) {
+                       double* lam_xi, double* g, double* lvn, double* lPn, double* B) {
     k_adj_derivs<<<adj_blocks(c, c.np), THREADS, 0, c.stream>>>(adj_params(c), xi, v, vstar, c.table, lJ, lam_P,
-                                                                 lam_v, lam_xe, mu, lam_xi, g, B, c.dev_status);
+                                                                 lam_v, lam_xe, mu, c.slide, lam_xi, g, lvn, lPn, B,
+                                                                 c.dev_status);
     ++c.launches;
 }
 
@@ -591,11 +631,6 @@ int launch_adj_jacobi(Ctx& c, const double* g, const double* B, const double* mu
 
 void launch_adj_axpy(Ctx& c, int64_t n, double* y, const double* x, double s) {
     k_adj_axpy<<<adj_blocks(c, n), THREADS, 0, c.stream>>>(n, y, x, s);
-    ++c.launches;
-}
-
-void launch_adj_slide_check(Ctx& c) {
-    k_adj_slide_count<<<adj_blocks(c, c.np), THREADS, 0, c.stream>>>(c.np, c.slide, c.dev_status);
     ++c.launches;
 }
 

@@ -1088,6 +1088,8 @@ pic_status adj_alloc(pic_ctx* ctx) {
     ALLOC(c.adj_xi, double, np3);
     ALLOC(c.adj_g, double, np3);
     ALLOC(c.adj_tmp, double, np3);
+    ALLOC(c.adj_vn, double, np3);
+    ALLOC(c.adj_Pn, double, np3);
     ALLOC(c.adj_B, double, 3 * np3);
     ALLOC(c.adj_F1, double, 4 * N);
     ALLOC(c.adj_W1, double, 4 * N);
@@ -1142,7 +1144,8 @@ void adj_sweep(Ctx& c, const double* xi_n, const double* v_n, const double* vsta
     double* ys = c.adj_ys;
     launch_helmholtz(c, c.adj_t, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, &y, &ys);
     launch_adj_mesh_out(c, y, c.adj_pn, c.adj_W1, c.adj_rho1, c.adj_F0, c.adj_W0, c.adj_rho0, c.adj_J);
-    launch_adj_derivs(c, xi_n, v_n, vstar, c.adj_J, c.adj_P, c.adj_v, c.adj_xe, c.adj_mu, c.adj_xi, c.adj_g, c.adj_B);
+    launch_adj_derivs(c, xi_n, v_n, vstar, c.adj_J, c.adj_P, c.adj_v, c.adj_xe, c.adj_mu, c.adj_xi, c.adj_g, c.adj_vn,
+                      c.adj_Pn, c.adj_B);
 }
 
 }  // namespace
@@ -1176,7 +1179,6 @@ pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_
         adj_in(c, lam_next->v, kin, c.adj_v, one);
         adj_in(c, lam_next->P, kin, c.adj_P, one);
         cudaMemsetAsync(c.adj_mu, 0, sizeof(double) * 3 * np, c.stream);
-        launch_adj_slide_check(c);
     }
     mesh_in(c, lam_next->phi, kin, c.adj_F1, N);
     mesh_in(c, lam_next->A, kin, c.adj_F1 + N, 3 * N);
@@ -1185,8 +1187,6 @@ pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_
     mesh_in(c, lam_next->rho, kin, c.adj_rho1, N);
     s = sync_results(ctx, "pic_step_vjp");
     if (s != PIC_OK) return s;
-    if (*c.host_status & DEV_ERR_SLIDE)
-        return fail(ctx, PIC_ERR_ARG, "pic_step_vjp: a component of this step slides on a knot (not differentiated)");
     // the transposed fixed point for mu, block-Jacobi
     const double tol = 1e-13;
     const int max_it = 60;
@@ -1210,12 +1210,8 @@ pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_
     adj_sweep(c, xi_n, v_n, vstar);
     if (np > 0) {
         adj_out(c, c.adj_xi, lam_prev->x, kout, tox);
-        adj_out(c, c.adj_g, lam_prev->v, kout, one);                    // beta's v^n = its v*
-        cudaMemcpyAsync(c.adj_tmp, c.adj_v, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
-        launch_adj_axpy(c, 3 * np, c.adj_tmp, c.adj_mu, 1.0);
-        cudaMemcpyAsync(c.adj_g, c.adj_P, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c.stream);
-        launch_adj_axpy(c, 3 * np, c.adj_g, c.adj_tmp, 1.0 / c.mass);   // P^{n+1} = P^n + ...: lam_P + lam_v1 / m
-        adj_out(c, c.adj_g, lam_prev->P, kout, one);
+        adj_out(c, c.adj_vn, lam_prev->v, kout, one);
+        adj_out(c, c.adj_Pn, lam_prev->P, kout, one);
         if (lam_prev->vprev) cudaMemsetAsync(lam_prev->vprev, 0, sizeof(double) * 3 * np, c.stream);
     }
     mesh_out(c, c.adj_F0, lam_prev->phi, kout, N);

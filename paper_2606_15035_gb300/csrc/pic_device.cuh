@@ -19,7 +19,6 @@ enum : int {
     DEV_ERR_TILE = 4,       // an orbit left the mesh tile computed for its block (not expected)
     DEV_ERR_TIMEOUT = 8,    // a bounded wait on an asynchronous copy gave up
     DEV_ERR_RANGE = 16,     // a deposit beyond the exact accumulator's range (deterministic mode)
-    DEV_ERR_SLIDE = 32,     // the step being differentiated has a component sliding on a knot
 };
 
 constexpr int MAX_SEGMENTS = 64;

@@ -178,7 +178,7 @@ struct Ctx {
     // adjoint (9 N), the level-(n+1) inputs and level-n outputs, the Helmholtz buffers, J's adjoint
     bool fresh_init = false;             // the state is pic_init's (no step or set_state since)
     double *adj_xe = nullptr, *adj_v = nullptr, *adj_P = nullptr, *adj_mu = nullptr, *adj_mu2 = nullptr;
-    double *adj_xi = nullptr, *adj_g = nullptr, *adj_B = nullptr, *adj_tmp = nullptr;
+    double *adj_xi = nullptr, *adj_g = nullptr, *adj_B = nullptr, *adj_tmp = nullptr, *adj_vn = nullptr, *adj_Pn = nullptr;
     double *adj_tab = nullptr, *adj_F1 = nullptr, *adj_W1 = nullptr, *adj_rho1 = nullptr;
     double *adj_t = nullptr, *adj_pn = nullptr, *adj_y = nullptr, *adj_ys = nullptr, *adj_J = nullptr;
     double *adj_F0 = nullptr, *adj_W0 = nullptr, *adj_rho0 = nullptr;
@@ -228,10 +228,9 @@ void launch_adj_mesh_out(Ctx& c, const double* y, const double* pn, const double
                          double* lF0, double* lW0, double* lrho0, double* lJ);
 void launch_adj_derivs(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lJ,
                        const double* lam_P, const double* lam_v, const double* lam_xe, const double* mu,
-                       double* lam_xi, double* g, double* B);
+                       double* lam_xi, double* g, double* lvn, double* lPn, double* B);
 int launch_adj_jacobi(Ctx& c, const double* g, const double* B, const double* mu, double* mu_new);
 void launch_adj_axpy(Ctx& c, int64_t n, double* y, const double* x, double s);
-void launch_adj_slide_check(Ctx& c);
 void launch_adj_deposit(Ctx& c, const double* xi, const double* lam_dep, double* lam_xi);
 void launch_energy_grad(Ctx& c, double* lF, double* lW);
 

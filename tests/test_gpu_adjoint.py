@@ -78,6 +78,83 @@ def test_one_step_vjp_matches_directional_differences(sim):
     s.close()
 
 
+def test_one_step_vjp_with_sliding_components(sim):
+    """Generic beams through a strong smooth vector potential, plus 64 particles placed within
+    1e-13 .. 3e-12 cells of a y knot and drifting onto it: the particle-local solves slide some
+    of their components onto the knot, and the adjoint differentiates those through the sliding
+    equations.  The direction leaves the near-knot particles' start positions and velocities
+    alone (their branch is decided within 1e-11 cells of the knot, far inside any difference
+    interval) and perturbs everything else, so the quotient stays on one branch of the map."""
+    import torch
+    from oracle import mesh as omesh
+    from oracle import orbit as oorbit
+    from oracle import pic as opic
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    n, L = w.n, w.L
+    ocfg = opic.Config(n=n, L=L, dt=0.1, picard_tol=1e-13, picard_max=30)
+    grid = ocfg.grid()
+    H = np.asarray(grid.H)
+    rng = np.random.default_rng(17)
+    npart, nnear = 2048, 64
+    xi = rng.uniform(0, 8, size=(npart, 3))
+    v = rng.normal(scale=0.01, size=(npart, 3))
+    v[:, 0] += 0.2 * rng.choice([-1.0, 1.0], size=npart)
+    k = rng.integers(0, 8, size=nnear).astype(float)
+    dk = 10.0 ** rng.uniform(-13, -11.5, size=nnear)
+    sg = rng.choice([-1.0, 1.0], size=nnear)
+    xi[:nnear, 1] = np.mod(k - sg * dk, 8.0)
+    v[:nnear, 1] = sg * dk * rng.uniform(0.5, 1.5, size=nnear) * H[1] / ocfg.dt
+    q = -1.0 / npart
+    o = opic.init(xi * H, v, q, abs(q), ocfg)
+    F = np.stack([omesh.project_out_null(rng.normal(size=grid.n), grid) for _ in range(3)])
+    for _ in range(2):
+        F = F + 0.25 * np.stack([omesh.lap(F[c], grid) * min(grid.H) ** 2 for c in range(3)])
+    A = omesh.curl(F, grid)
+    A *= 0.2 / np.abs(A).max()
+    o = opic.replace(o, A=A, P=o.m * o.v + o.q * oorbit.point_gather(A, o.xi, grid).T)
+    x = opic.positions(o, ocfg)
+    cfg = sim.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-13, picard_max=30)
+    s = sim.PicSim(cfg, x, o.v, o.q, o.m)
+    st = s.get_state()
+    st.x, st.v, st.P, st.vprev = x, o.v, o.P, o.vprev
+    st.phi, st.psi, st.A, st.U, st.rho = o.phi, o.psi, o.A, o.U, o.rho
+    s.set_state(st)
+    base = s.get_state_device()
+    assert s.step(1).converged
+    _, bits = s.accepted()
+    assert ((bits & 7) != 0).sum() >= 1 and not ((bits[nnear:] & 7) != 0).any()
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    d = {kk: 1e-3 * torch.randn(t.shape, generator=gen, device="cuda", dtype=torch.float64) for kk, t in base.items()}
+    d["vprev"].zero_()
+    d["P"] *= o.m
+    for kk in ("x", "v"):
+        d[kk].reshape(3, npart)[:, :nnear] = 0.0
+    lam = {kk: torch.randn(t.shape, generator=gen, device="cuda", dtype=torch.float64) for kk, t in base.items()}
+    lam["vprev"].zero_()
+    keys = ("x", "v", "P", "phi", "psi", "rho", "A", "U")
+    Lv = torch.tensor(L, dtype=torch.float64, device="cuda")
+
+    def step_from(stt):
+        s.set_state_device(stt)
+        assert s.step(1).converged
+        return s.get_state_device(), s.accepted()[1]
+
+    h = 1e-5
+    plus, bp = step_from({kk: base[kk] + h * d[kk] for kk in base})
+    minus, bm = step_from({kk: base[kk] - h * d[kk] for kk in base})
+    assert np.array_equal(bp & 7, bits & 7) and np.array_equal(bm & 7, bits & 7)   # one branch
+    diff = {kk: plus[kk] - minus[kk] for kk in base}
+    ddx = diff["x"].reshape(3, -1)
+    diff["x"] = (((ddx + 0.5 * Lv[:, None]) % Lv[:, None]) - 0.5 * Lv[:, None]).reshape(-1)
+    fd = _dot(lam, diff, keys) / (2 * h)
+    s.set_state_device(base)
+    assert s.step(1).converged
+    lam_prev, info = s.step_vjp(lam)
+    adj = _dot(lam_prev, d, keys)
+    assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd, info.iterations)
+    s.close()
+
+
 def _family(n, L, ppb, v0, eps, seed):
     """Uniform start positions and the beams' signs, for x0(eps) = xu + eps sin(k1 xu) e_x and
     v0 = +-v0 e_x, exactly as pic_inputs.random_twostream builds them."""
