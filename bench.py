@@ -524,8 +524,12 @@ def main():
         clk = sampler.stop() if sampler else None
         pr = sm.profile(False)
         t_ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
+        ev_h, ej_h, kind_h = sm.residual_history()
+        kinds = {0: "fp64", 1: "fp32", 2: "fp32-pair"}
+        fin = lambda z: float(z) if np.isfinite(z) else None   # strict JSON: no Infinity
+        history = [[fin(a), fin(b), kinds[int(k)]] for a, b, k in zip(ev_h, ej_h, kind_h)]
         return {"sim": sm, "prof": pr, "ms": t_ms, "drift": drift, "clocks": clk,
-                "iters": it / max(done, 1), "iters32": it32 / max(done, 1)}
+                "iters": it / max(done, 1), "iters32": it32 / max(done, 1), "history": history}
 
     head = timed(args.precision, True)
     s, prof, ms = head["sim"], head["prof"], head["ms"]
@@ -584,6 +588,7 @@ def main():
         other = {"precision": oname, "value": whole_job_rate(w.n_particles, world, args.steps, o["ms"] / 1e3),
                  "unit": UNIT, "ms_per_step": o["ms"] / args.steps, "relative_energy_drift": o["drift"],
                  "mean_picard_iterations": o["iters"], "mean_fp32_iterations": o["iters32"],
+                 "residual_history_last_step": o["history"],
                  "kernel_shares": kernel_shares(po, o["ms"]),
                  "fp64_push_roofline": fp64_push_roofline(po, w.name),
                  "fp32_push_roofline": fp32_push_roofline(po, w.name, w.n_particles, hbm_gbs, hbm_note)}
@@ -618,6 +623,7 @@ def main():
                              f"per GPU: x, v, P, v^(n-1), iterate)",
                        "mean_picard_iterations": head["iters"], "mean_fp32_iterations": head["iters32"],
                        "relative_energy_drift": head["drift"],
+                       "residual_history_last_step": head["history"],
                        "drift_definition": "max over the W + K steps of |E^n - E^0| / E^0, E^0 at pic_init; "
                                            "the energy is evaluated after every step, inside the timed region"},
             "roofline": roofline,
