@@ -65,8 +65,14 @@ MIN_FLOPS_PER_PIECE = 398
 # write the new increment 12).
 BYTES32_PER_PARTICLE = 52
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel version in the tree,
-# keyed by kernel and workload (None: not captured for this version).
-NCU_TRAFFIC = {}
+# keyed by kernel and workload, with how the figure was obtained (absent: not captured for this
+# version).  The 128^3 run is too large for a multi-pass capture, so its k_push figure is the
+# 32^3 capture (2,097,152 particles, third Picard iteration) scaled by the particle count: the
+# kernel's traffic is its particle streams, 141.7 B per particle-iteration there.
+NCU_TRAFFIC = {
+    ("k_push", "twostream-32c-2M"): (297.07e6, "ncu capture, one launch (dram read 259.32 MB + write 37.75 MB)"),
+    ("k_push", "twostream-128c-134M"): (297.07e6 * 64, "the 32^3 capture scaled by particles (x 64)"),
+}
 
 
 def parse():
@@ -427,8 +433,9 @@ def fp64_push_roofline(prof, workload):
                            "piece + 150 per scatter piece",
             "frac_survey_minimum": achieved_min / FP64_PEAK_TFLOPS,
             "survey_minimum_basis": "86 per particle + 398 per orbit piece (the survey's per-orbit estimate)",
-            "traffic": NCU_TRAFFIC.get(("k_push", workload)),
+            "traffic": NCU_TRAFFIC.get(("k_push", workload), (None, None))[0],
             "traffic_unit": "DRAM bytes per launch (ncu dram read + write)",
+            "traffic_source": NCU_TRAFFIC.get(("k_push", workload), (None, "not captured"))[1],
             "kernel": "k_push (fused FP64 orbit push + next-orbit current scatter, Picard iterations)",
             "peak_note": "FP64 ALU, of derived: 152 SMs x 4 flop/clk x 2070 MHz (the live probe is in fma_probe)",
             "launches": int(prof.push_launches), "ms_per_launch": prof.push_ms / prof.push_launches,
@@ -443,7 +450,7 @@ def fp32_push_roofline(prof, workload, npart, hbm_gbs, hbm_note):
     bytes_per_launch = float(BYTES32_PER_PARTICLE) * npart
     gbs = bytes_per_launch * prof.push32_launches / (prof.push32_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
-            "traffic": NCU_TRAFFIC.get(("k_push32", workload)), "peak_note": hbm_note,
+            "traffic": NCU_TRAFFIC.get(("k_push32", workload), (None, None))[0], "peak_note": hbm_note,
             "kernel": "k_push32 (FP32 orbit push + next-orbit current scatter)",
             "bytes_per_particle_iteration": BYTES32_PER_PARTICLE, "launches": int(prof.push32_launches),
             "ms_per_launch": prof.push32_ms / prof.push32_launches,

@@ -305,8 +305,9 @@ pic_status pic_set_wait_limit(pic_ctx* ctx, int64_t cycles);
  * (the Helmholtz operator is symmetric).  Positions' adjoints are per physical unit.  The
  * adjoint of v^{n-1} is zero (it only sets the first Picard iterate). */
 typedef struct {
-    int32_t iterations;   /* block-Jacobi iterations of the transposed fixed point (+ the final sweep) */
-    double residual;      /* its last relative change ||mu_new - mu|| / ||mu_new|| */
+    int32_t iterations;   /* sweeps (applications of F^T) made by the transposed solve */
+    double residual;      /* its final ||P r|| / ||mu||: r = F_v*^T(lambda' + mu) - mu the residual,
+                             P the preconditioner, so the size of one more correction */
 } pic_vjp_info;
 
 /* lam_prev = (d state^{n+1} / d state^n)^T lam_next for the step that the last pic_step
@@ -315,8 +316,13 @@ typedef struct {
  * lam_prev are not written).  Needs closed-form linear orbits and central differences.  A
  * component that slid onto a knot in that step is differentiated through the sliding
  * equations (its iterate is the landing velocity 2 d H / dt - v^n, its momentum m v + q A_h).
- * PIC_ERR_NO_CONVERGENCE if the transposed fixed point does not reach 1e-11 in 100 iterations.
- * Allocates its work buffers (about 45 np + 50 ncell doubles) on first use. */
+ * The transposed fixed point is solved by restarted GMRES (restart length 40, fewer when its
+ * basis would pass 4 GiB), preconditioned with the transpose of the forward iteration's
+ * splitting: the particles that the step solved locally get their 3 x 3 block
+ * (I - (dG_i/dv_i)^T)^{-1}, all others the identity.  PIC_ERR_NO_CONVERGENCE if it does not
+ * reach 1e-11 in 400 sweeps (the message lists the residual at each restart).  Allocates its
+ * work buffers (about 51 np + 50 ncell doubles, plus the basis of 3 np (restart + 1) doubles)
+ * on first use. */
 pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_state_view* lam_prev,
                         pic_vjp_info* info);
 

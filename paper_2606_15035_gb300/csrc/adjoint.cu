@@ -21,11 +21,17 @@
 //      forward-mode dual numbers through the same closed-form orbit integrals (dual.cuh), six
 //      directions, with the mesh adjoints and fields held fixed.  beta = dt (v* + v^n) / (2 H)
 //      gives the adjoints of v* and v^n.
-// The transposed fixed point is solved by block-Jacobi: per particle the 3 x 3 block
-// B = dG_i / dv*_i (fields fixed, from the same dual passes) is inverted,
-//     mu_new = (I - B^T)^{-1} (g(mu) - B^T mu),
-// g(mu) being step 3's adjoint of v*.  That is the transposed counterpart of the forward
-// solve's particle-local solves: the remaining coupling is the weak one through the fields.
+// The transposed fixed point (I - K) mu = b0, g(mu) = K mu + b0 being step 3's adjoint of v*,
+// is solved by restarted GMRES with right preconditioning.  The preconditioner is the transpose
+// of the forward iteration's own splitting: a particle that the step solved locally (its
+// slide byte's SLIDE_CREPT bit) gets its 3 x 3 block (I - B^T)^{-1}, B = dG_i / dv*_i with the
+// fields fixed (from the same dual passes); every other particle gets the identity, as the plain
+// Picard update treats it.  The stationary iteration with this splitting is the transposed
+// linearisation of the forward solve, so its spectral radius is that of the forward iteration
+// at the accepted step (below one, since the step converged), and the preconditioned operator's
+// spectrum lies in a disc around 1 of that radius.  Within a restart cycle GMRES's residual is
+// never above the stationary iteration's, and it is far below it where the forward iteration
+// itself converged slowly.
 //
 // Sliding components (the step committed them by the sliding equations, §9 of the notes on the
 // local solve): their iterate is the explicit landing velocity v*_a = 2 d_a H_a / dt - v^n_a,
@@ -41,6 +47,7 @@
 #include <string>
 
 #include "pic_internal.h"
+#include "particle_common.cuh"
 #include "dual.cuh"
 
 namespace pic {
@@ -438,65 +445,94 @@ __global__ void __launch_bounds__(THREADS) k_adj_derivs(AdjParams ap, const doub
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const bool drop = sl || ((sb >> d) & 1u);
+                const bool drop = sl || ((sb >> d) & 1u) || !(sb & SLIDE_CREPT);
                 Bout[(3 * a + d) * np + i] = drop ? 0.0 : dB[a][d];
             }
         }
     }
 }
 
-// mu_new = (I - B^T)^{-1} (g - B^T mu) per particle; partial sums of |mu_new - mu|^2, |mu_new|^2.
-__global__ void k_adj_jacobi(int64_t np, const double* __restrict__ g, const double* __restrict__ B,
-                             const double* __restrict__ mu, double* __restrict__ mu_new, double* __restrict__ partials,
-                             int* __restrict__ status) {
-    __shared__ double sm[32];
-    double num = 0.0, den = 0.0;
-    ADJ_LOOP(i, np) {
-        double M[3][3], r[3];
+// x = (I - B^T)^{-1} r for particle i's 3 x 3 block (Cramer's rule); false if singular.
+__device__ __forceinline__ bool solve_block(const double* __restrict__ B, int64_t np, int64_t i, const double r[3],
+                                            double x[3]) {
+    double M[3][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            r[a] = g[a * np + i];
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double bt = B[(3 * d + a) * np + i];        // (B^T)[a][d] = B[d][a]
-                M[a][d] = (a == d ? 1.0 : 0.0) - bt;
-                r[a] -= bt * mu[d * np + i];
-            }
-        }
-        // Cramer's rule on the 3 x 3 system M x = r
-        const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
-                           M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-        double x[3];
-        if (!(fabs(det) > 1e-300)) {
-            atomicOr(status, DEV_ERR_NONFINITE);
-            x[0] = x[1] = x[2] = 0.0;
-        } else {
-#pragma unroll
-            for (int col = 0; col < 3; ++col) {
-                double Mc[3][3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) Mc[a][d] = d == col ? r[a] : M[a][d];
-                const double dc = Mc[0][0] * (Mc[1][1] * Mc[2][2] - Mc[1][2] * Mc[2][1]) -
-                                  Mc[0][1] * (Mc[1][0] * Mc[2][2] - Mc[1][2] * Mc[2][0]) +
-                                  Mc[0][2] * (Mc[1][0] * Mc[2][1] - Mc[1][1] * Mc[2][0]);
-                x[col] = dc / det;
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double dlt = x[a] - mu[a * np + i];
-            num += dlt * dlt;
-            den += x[a] * x[a];
-            mu_new[a * np + i] = x[a];
-        }
+        for (int d = 0; d < 3; ++d) M[a][d] = (a == d ? 1.0 : 0.0) - B[(3 * d + a) * np + i];   // (B^T)[a][d] = B[d][a]
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (!(fabs(det) > 1e-300)) {
+        x[0] = x[1] = x[2] = 0.0;
+        return false;
     }
-    double rs = block_sum(num, sm);
-    if (threadIdx.x == 0) partials[S_EV_NUM * MAX_BLOCKS + blockIdx.x] = rs;
-    rs = block_sum(den, sm);
-    if (threadIdx.x == 0) partials[S_EV_DEN * MAX_BLOCKS + blockIdx.x] = rs;
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        double Mc[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Mc[a][d] = d == col ? r[a] : M[a][d];
+        const double dc = Mc[0][0] * (Mc[1][1] * Mc[2][2] - Mc[1][2] * Mc[2][1]) -
+                          Mc[0][1] * (Mc[1][0] * Mc[2][2] - Mc[1][2] * Mc[2][0]) +
+                          Mc[0][2] * (Mc[1][0] * Mc[2][1] - Mc[1][1] * Mc[2][0]);
+        x[col] = dc / det;
+    }
+    return true;
+}
+
+// The preconditioner of the transposed solve, z = P r: per particle (I - B^T)^{-1} r, with B
+// zero outside the particles the step solved locally (there P = I).
+__global__ void k_adj_precond(int64_t np, const double* __restrict__ B, const double* __restrict__ r,
+                              double* __restrict__ z, int* __restrict__ status) {
+    ADJ_LOOP(i, np) {
+        double ri[3], x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ri[a] = r[a * np + i];
+        if (!solve_block(B, np, i, ri, x)) atomicOr(status, DEV_ERR_NONFINITE);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) z[a * np + i] = x[a];
+    }
+}
+
+// w = z - (g - b0): the transposed fixed point's operator (I - K) applied to z, g = K z + b0
+// being the sweep's output at mu = z.
+__global__ void k_adj_apply(int64_t n, const double* __restrict__ z, const double* __restrict__ g,
+                            const double* __restrict__ b0, double* __restrict__ w) {
+    ADJ_LOOP(i, n) w[i] = z[i] - g[i] + b0[i];
+}
+
+// part[k * gridDim.x + b] = block b's share of w . V_k, k < nv (V_k at V + k ldv).
+__global__ void k_adj_mdot(int64_t n, const double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int nv,
+                           double* __restrict__ part) {
+    __shared__ double sm[32];
+    for (int k = 0; k < nv; ++k) {
+        double s = 0.0;
+        const double* vk = V + k * ldv;
+        ADJ_LOOP(i, n) s += w[i] * vk[i];
+        s = block_sum(s, sm);
+        if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// out[k] = sum over the nb block shares of dot k, in a fixed order (one block per dot).
+__global__ void k_adj_mdot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[blockIdx.x * nb + b];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// w += sign * sum_k h[k] V_k, k < nv (h on the device).
+__global__ void k_adj_combine(int64_t n, double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int nv,
+                              const double* __restrict__ h, double sign) {
+    ADJ_LOOP(i, n) {
+        double s = 0.0;
+        for (int k = 0; k < nv; ++k) s += h[k] * V[k * ldv + i];
+        w[i] += sign * s;
+    }
 }
 
 // Elementwise helpers.
@@ -622,11 +658,28 @@ void launch_adj_derivs(Ctx& c, const double* xi, const double* v, const double* 
     ++c.launches;
 }
 
-int launch_adj_jacobi(Ctx& c, const double* g, const double* B, const double* mu, double* mu_new) {
-    const int nb = adj_blocks(c, c.np);
-    k_adj_jacobi<<<nb, THREADS, 0, c.stream>>>(c.np, g, B, mu, mu_new, c.partials, c.dev_status);
+void launch_adj_precond(Ctx& c, const double* B, const double* r, double* z) {
+    k_adj_precond<<<adj_blocks(c, c.np), THREADS, 0, c.stream>>>(c.np, B, r, z, c.dev_status);
     ++c.launches;
-    return nb;
+}
+
+void launch_adj_apply(Ctx& c, int64_t n, const double* z, const double* g, const double* b0, double* w) {
+    k_adj_apply<<<adj_blocks(c, n), THREADS, 0, c.stream>>>(n, z, g, b0, w);
+    ++c.launches;
+}
+
+void launch_adj_mdot(Ctx& c, int64_t n, const double* w, const double* V, int64_t ldv, int nv, double* part,
+                     double* out) {
+    const int nb = adj_blocks(c, n);
+    k_adj_mdot<<<nb, THREADS, 0, c.stream>>>(n, w, V, ldv, nv, part);
+    k_adj_mdot_final<<<nv, THREADS, 0, c.stream>>>(part, nb, out);
+    c.launches += 2;
+}
+
+void launch_adj_combine(Ctx& c, int64_t n, double* w, const double* V, int64_t ldv, int nv, const double* h,
+                        double sign) {
+    k_adj_combine<<<adj_blocks(c, n), THREADS, 0, c.stream>>>(n, w, V, ldv, nv, h, sign);
+    ++c.launches;
 }
 
 void launch_adj_axpy(Ctx& c, int64_t n, double* y, const double* x, double s) {

@@ -9,8 +9,8 @@ namespace pic {
 
 constexpr uint8_t SLIDE_CREPT = 8;    // slide-byte bit 3: solved locally earlier in this step
 constexpr double SLOW_RATIO = 0.25;   // a plain particle whose change did not shrink below this
-constexpr double SLOW_FLOOR = 1e-12;  // of the previous one (and exceeds this x its speed) is
-                                      // solved locally from then on
+                                      // of the previous one (and exceeds the launch's floor
+                                      // times its speed) is solved locally from then on
 
 // Orbit-piece classes for ordering the particles of a chunk: 1, 2, 3, >= 4 pieces, and a
 // last class for the threads past the end of the particle array.

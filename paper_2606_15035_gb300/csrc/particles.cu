@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
                         dold = fmax(dold, fabs(vi[a] - vnew[a * np + i]));   // v^p - v^{p-1}
                     }
                     const double spd = sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
-                    slow = dn > SLOW_RATIO * dold && dn > SLOW_FLOOR * spd;
+                    slow = dn > SLOW_RATIO * dold && dn > p.slow_floor * spd;
                 }
                 const bool creep = p.accel && (is_creeping(xk, beta_it) || (slide[i] & SLIDE_CREPT) || slow);
                 if (creep_flag) creep_flag[i] = creep ? 1 : 0;   // deterministic mode: k_local walks the flags
@@ -1308,6 +1308,7 @@ StepParams make_params(const Ctx& c) {
     p.nq = c.cfg.nq;
     p.accel = c.cfg.picard_accel;
     p.hist = 0;
+    p.slow_floor = c.run.after32 ? SLOW_FLOOR_AFTER32 : SLOW_FLOOR;
     p.order = c.cfg.shape_order;
     p.koff = (c.cfg.shape_order % 2 == 0) ? 0.5 : 0.0;
     p.det = c.cfg.deterministic;

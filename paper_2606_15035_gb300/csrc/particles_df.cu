@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_push_df(ParamsDF pd, const doubl
                     dold = fmax(dold, ::fabs(vi[a] - vnew[a * np + i]));
                 }
                 const double spd = sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
-                slow = dn > SLOW_RATIO * dold && dn > SLOW_FLOOR * spd;
+                slow = dn > SLOW_RATIO * dold && dn > pd.p.slow_floor * spd;
             }
             const bool creep = p.accel && (is_creeping(xk, beta_it) || (slide[i] & SLIDE_CREPT) || slow);
             if (creep_flag) creep_flag[i] = creep ? 1 : 0;

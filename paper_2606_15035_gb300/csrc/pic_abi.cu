@@ -598,8 +598,13 @@ pic_status iter_finish(pic_ctx* ctx) {
                 ProfScope ps(c, PH_SCATTER);
                 launch_first_scatter(c, c.J[r.cur], c.vnew);   // also copies the iterate into vit
             }
+            // the previous FP32 iterate as v^{p-1}: the first FP64 iteration already sends the
+            // particles that the FP32 loop left unconverged (a change that did not shrink, above
+            // the FP32 rounding) to the particle-local solve
+            launch_from32(c, c.vnew32, c.vnew);
             r.fp32 = false;
-            r.hist = false;
+            r.hist = c.cfg.picard_accel != 0;
+            r.after32 = true;
             r.pair = c.table_pair != nullptr;   // FP32-pair refinement next, if configured
         }
     } else {
@@ -647,8 +652,10 @@ pic_status iter_finish(pic_ctx* ctx) {
         std::swap(c.vit, c.vnew);
         // vnew now holds v^p, the iterate before the next one.  After an FP32 phase the first
         // FP64 change is the FP32 rounding of each particle, not its own contraction: the
-        // slow-particle test starts one FP64 iteration later.
+        // second FP64 iteration skips the slow-particle test (the first ran it against the last
+        // FP32 change, above the rounding floor), the third resumes it.
         ++r.p64;
+        r.after32 = false;
         r.hist = r.p64 >= (r.began32 ? 2 : 1);
         r.rotate();
     }
@@ -1103,6 +1110,14 @@ pic_status adj_alloc(pic_ctx* ctx) {
     ALLOC(c.adj_W0, double, 4 * N);
     ALLOC(c.adj_rho0, double, N);
     ALLOC(c.adj_tab, double, 9 * N);
+    // the transposed solve's restart length: 40, or fewer where the basis would pass 4 GiB
+    const size_t vec = sizeof(double) * (size_t)np3;
+    c.adj_m = (int)std::max<size_t>(4, std::min<size_t>(40, ((size_t)4 << 30) / vec - 1));
+    ALLOC(c.adj_b0, double, np3);
+    ALLOC(c.adj_w, double, np3);
+    ALLOC(c.adj_V, double, (size_t)(c.adj_m + 1) * np3);
+    ALLOC(c.adj_h, double, 2 * (c.adj_m + 2));
+    ALLOC(c.adj_part, double, (size_t)(c.adj_m + 2) * MAX_BLOCKS);
     return check_cuda(ctx, "adjoint buffers");
 }
 
@@ -1148,6 +1163,134 @@ void adj_sweep(Ctx& c, const double* xi_n, const double* v_n, const double* vsta
                       c.adj_Pn, c.adj_B);
 }
 
+// The transposed fixed point (I - K) mu = b0 (g(mu) = K mu + b0 is a sweep's adjoint of v*) by
+// restarted GMRES, right-preconditioned with the forward step's splitting (launch_adj_precond).
+// Each restart cycle starts from the true residual r = g(mu) - mu and checks |P r| / |mu|, the
+// size of a preconditioned correction relative to mu, against tol.  On success c.adj_mu holds
+// mu and the last sweep's outputs are those at mu.
+pic_status adj_solve(pic_ctx* ctx, const double* xi_n, const double* v_n, const double* vstar, double tol,
+                     int max_sweeps, int* sweeps_out, double* res_out) {
+    Ctx& c = ctx->c;
+    const int64_t n = 3 * c.np;
+    const int m = c.adj_m;
+    const size_t vb = sizeof(double) * (size_t)n;
+    double* V = c.adj_V;
+    double* sol = c.adj_mu2;
+    std::vector<double> hb(2 * (m + 2), 0.0);
+    auto fetch = [&](int count) {
+        cudaMemcpyAsync(hb.data(), c.adj_h, sizeof(double) * count, cudaMemcpyDeviceToHost, c.stream);
+        return sync_results(ctx, "pic_step_vjp");
+    };
+    int sweeps = 0;
+    cudaMemsetAsync(c.adj_mu, 0, vb, c.stream);
+    adj_sweep(c, xi_n, v_n, vstar);
+    ++sweeps;
+    cudaMemcpyAsync(c.adj_b0, c.adj_g, vb, cudaMemcpyDeviceToDevice, c.stream);
+    cudaMemsetAsync(sol, 0, vb, c.stream);
+    launch_adj_mdot(c, n, c.adj_b0, c.adj_b0, n, 1, c.adj_part, c.adj_h);
+    pic_status s = fetch(1);
+    if (s != PIC_OK) return s;
+    if (!std::isfinite(hb[0])) return fail(ctx, PIC_ERR_NONFINITE, "pic_step_vjp: non-finite adjoint");
+    *sweeps_out = sweeps;
+    *res_out = 0.0;
+    if (hb[0] == 0.0) return PIC_OK;   // mu = 0, and the sweep just made is at mu
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gam(m + 1), y(m);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    std::string trace;
+    double res = INFINITY, best = INFINITY, target_ratio = 1e-4;
+    for (int cycle = 0;; ++cycle) {
+        // the true residual r = g(mu) - mu (b0 at mu = 0) in V_0, and the check
+        if (cycle == 0) {
+            cudaMemcpyAsync(V, c.adj_b0, vb, cudaMemcpyDeviceToDevice, c.stream);
+        } else {
+            cudaMemcpyAsync(c.adj_mu, sol, vb, cudaMemcpyDeviceToDevice, c.stream);
+            adj_sweep(c, xi_n, v_n, vstar);
+            ++sweeps;
+            launch_scale_copy(c, V, c.adj_g, n, 1.0);
+            launch_adj_axpy(c, n, V, sol, -1.0);
+        }
+        launch_adj_precond(c, c.adj_B, V, c.adj_w);
+        launch_adj_mdot(c, n, V, V, n, 1, c.adj_part, c.adj_h);
+        launch_adj_mdot(c, n, c.adj_w, c.adj_w, n, 1, c.adj_part, c.adj_h + 1);
+        launch_adj_mdot(c, n, sol, sol, n, 1, c.adj_part, c.adj_h + 2);
+        s = fetch(3);
+        if (s != PIC_OK) return s;
+        const double beta = std::sqrt(hb[0]);
+        res = cycle == 0 ? INFINITY : (hb[2] > 0.0 ? std::sqrt(hb[1] / hb[2]) : (hb[1] > 0.0 ? INFINITY : 0.0));
+        if (!std::isfinite(beta) || (cycle > 0 && std::isnan(res)))
+            return fail(ctx, PIC_ERR_NONFINITE, "pic_step_vjp: non-finite adjoint");
+        best = std::min(best, res);
+        if (cycle > 0) {
+            char buf[48];
+            std::snprintf(buf, sizeof(buf), "%s%d: %.2e", trace.empty() ? "" : ", ", sweeps, res);
+            trace += buf;
+        }
+        if (res <= tol || beta == 0.0) break;
+        if (sweeps >= max_sweeps) {
+            return fail(ctx, PIC_ERR_NO_CONVERGENCE,
+                        "pic_step_vjp: the transposed fixed point did not converge (sweeps: residual " + trace + ")");
+        }
+        // the reduction of |r| this cycle aims at: enough for tol, if the ratio of the checked
+        // residual to |r| stays as it is
+        if (cycle > 0) target_ratio = std::min(1e-4, std::max(1e-10, 0.25 * tol / res));
+        launch_scale_copy(c, V, V, n, 1.0 / beta);
+        std::fill(gam.begin(), gam.end(), 0.0);
+        gam[0] = beta;
+        int j = 0;
+        while (j < m && sweeps < max_sweeps) {
+            double* vj = V + (size_t)j * n;
+            double* vj1 = V + (size_t)(j + 1) * n;
+            launch_adj_precond(c, c.adj_B, vj, c.adj_mu);   // z_j = P v_j
+            adj_sweep(c, xi_n, v_n, vstar);
+            ++sweeps;
+            launch_adj_apply(c, n, c.adj_mu, c.adj_g, c.adj_b0, vj1);   // (I - K) z_j
+            // classical Gram--Schmidt, twice
+            launch_adj_mdot(c, n, vj1, V, n, j + 1, c.adj_part, c.adj_h);
+            launch_adj_combine(c, n, vj1, V, n, j + 1, c.adj_h, -1.0);
+            launch_adj_mdot(c, n, vj1, V, n, j + 1, c.adj_part, c.adj_h + (m + 2));
+            launch_adj_combine(c, n, vj1, V, n, j + 1, c.adj_h + (m + 2), -1.0);
+            launch_adj_mdot(c, n, vj1, vj1, n, 1, c.adj_part, c.adj_h + (m + 1));
+            s = fetch(2 * (m + 2));
+            if (s != PIC_OK) return s;
+            for (int k = 0; k <= j; ++k) Hij(k, j) = hb[k] + hb[m + 2 + k];
+            const double hn = std::sqrt(hb[m + 1]);
+            if (!std::isfinite(hn)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step_vjp: non-finite adjoint");
+            Hij(j + 1, j) = hn;
+            if (hn > 0.0) launch_scale_copy(c, vj1, vj1, n, 1.0 / hn);
+            for (int k = 0; k < j; ++k) {
+                const double a = Hij(k, j), b = Hij(k + 1, j);
+                Hij(k, j) = cs[k] * a + sn[k] * b;
+                Hij(k + 1, j) = -sn[k] * a + cs[k] * b;
+            }
+            const double a = Hij(j, j), b = Hij(j + 1, j), rr = std::hypot(a, b);
+            cs[j] = rr > 0.0 ? a / rr : 1.0;
+            sn[j] = rr > 0.0 ? b / rr : 0.0;
+            Hij(j, j) = rr;
+            Hij(j + 1, j) = 0.0;
+            gam[j + 1] = -sn[j] * gam[j];
+            gam[j] = cs[j] * gam[j];
+            ++j;
+            if (std::fabs(gam[j]) <= target_ratio * beta || hn == 0.0) break;
+        }
+        // mu += P V y, H y = gam (upper triangular)
+        for (int k = j - 1; k >= 0; --k) {
+            double t = gam[k];
+            for (int l = k + 1; l < j; ++l) t -= Hij(k, l) * y[l];
+            y[k] = Hij(k, k) != 0.0 ? t / Hij(k, k) : 0.0;
+        }
+        cudaMemcpyAsync(c.adj_h, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, c.stream);
+        cudaMemsetAsync(c.adj_w, 0, vb, c.stream);
+        launch_adj_combine(c, n, c.adj_w, V, n, j, c.adj_h, 1.0);
+        launch_adj_precond(c, c.adj_B, c.adj_w, c.adj_mu);
+        launch_adj_axpy(c, n, sol, c.adj_mu, 1.0);
+        s = sync_results(ctx, "pic_step_vjp");   // y is host memory
+        if (s != PIC_OK) return s;
+    }
+    *sweeps_out = sweeps;
+    *res_out = res;
+    return PIC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1187,34 +1330,17 @@ pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_
     mesh_in(c, lam_next->rho, kin, c.adj_rho1, N);
     s = sync_results(ctx, "pic_step_vjp");
     if (s != PIC_OK) return s;
-    // the transposed fixed point for mu, block-Jacobi, to 1e-11 relative: the sweep's own
-    // rounding (FP64 atomics in an order that varies between calls) sets a floor near 1e-14 of
-    // mu per sweep, which many sweeps over 10^5-10^6 particles can raise towards 1e-12
-    const double tol = 1e-11;
-    const int max_it = 100;
-    int it = 0;
-    double res = 0.0, best = INFINITY;
-    for (it = 0; np > 0 && it < max_it; ++it) {
-        adj_sweep(c, xi_n, v_n, vstar);
-        const int nb = launch_adj_jacobi(c, c.adj_g, c.adj_B, c.adj_mu, c.adj_mu2);
-        launch_finalize(c, S_EV_NUM, 2, nb, false);
-        s = sync_results(ctx, "pic_step_vjp");
+    // the transposed fixed point for mu, to 1e-11 relative: the sweep's own rounding (FP64
+    // atomics in an order that varies between calls) sets a floor near 1e-14 of mu per sweep
+    int sweeps = 0;
+    double res = 0.0;
+    if (np > 0) {
+        s = adj_solve(ctx, xi_n, v_n, vstar, 1e-11, 400, &sweeps, &res);
         if (s != PIC_OK) return s;
-        const double num = c.host_results[S_EV_NUM], den = c.host_results[S_EV_DEN];
-        res = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
-        std::swap(c.adj_mu, c.adj_mu2);
-        if (!std::isfinite(res)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step_vjp: non-finite adjoint");
-        best = std::min(best, res);
-        if (res <= tol) break;
+    } else {
+        adj_sweep(c, xi_n, v_n, vstar);   // the mesh-only adjoint
+        sweeps = 1;
     }
-    if (np > 0 && it >= max_it) {
-        char buf[160];
-        std::snprintf(buf, sizeof(buf), "pic_step_vjp: the transposed fixed point did not converge (last %.3e, best %.3e)",
-                      res, best);
-        return fail(ctx, PIC_ERR_NO_CONVERGENCE, buf);
-    }
-    // the outputs at the converged mu
-    adj_sweep(c, xi_n, v_n, vstar);
     if (np > 0) {
         adj_out(c, c.adj_xi, lam_prev->x, kout, tox);
         adj_out(c, c.adj_vn, lam_prev->v, kout, one);
@@ -1229,7 +1355,7 @@ pic_status pic_step_vjp(pic_ctx* ctx, const pic_state_view* lam_next, const pic_
     s = sync_results(ctx, "pic_step_vjp");
     if (s != PIC_OK) return s;
     if (info) {
-        info->iterations = it + 1;
+        info->iterations = sweeps;
         info->residual = res;
     }
     return PIC_OK;

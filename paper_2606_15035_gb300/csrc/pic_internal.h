@@ -50,6 +50,14 @@ enum Slot : int {
 };
 
 constexpr int MAX_BLOCKS = 4096;
+
+// Floors of the slow-particle test of the particle-local solves, as fractions of the speed: a
+// particle is slow when its change did not shrink below SLOW_RATIO of the previous one and
+// exceeds the floor.  In the first FP64 iteration after the FP32 ones the previous change is
+// the last FP32 one, so the floor sits above the FP32 iterate's rounding (increments good to
+// ~1e-10 of the speed): only particles that the FP32 loop left unconverged pass it.
+constexpr double SLOW_FLOOR = 1e-12;
+constexpr double SLOW_FLOOR_AFTER32 = 1e-8;
 constexpr int THREADS = 256;
 
 struct StepParams {
@@ -61,6 +69,7 @@ struct StepParams {
     int nq;                    // Gauss points (Gauss quadrature only)
     int accel;                 // particle-local solves for creeping particles
     int hist;                  // vnew holds v^{p-1} (slow particles are found against it)
+    double slow_floor;         // a slow particle's change also exceeds this times its speed
     int order;                 // B-spline degree r of the shape (1, 2, 3)
     double koff;               // knot offset: 0 (odd r, knots at the integers) or 0.5 (even r)
     int det;                   // deterministic mode: deposits go to acc (exact, order independent)
@@ -74,7 +83,8 @@ constexpr int FFT_MAX_STAGES = 16;
 struct StepRun {
     int cur = 0, prev = 1, next = 2;   // J buffers: current iterate, previous, next
     bool fp32 = false;                 // the next iteration runs in FP32 (PIC_MIXED)
-    bool hist = false;                 // vnew holds the previous FP64 iterate v^{p-1}
+    bool hist = false;                 // vnew holds the previous iterate v^{p-1}
+    bool after32 = false;              // the iteration in flight is the first FP64 one after FP32
     bool began32 = false;              // the step began with FP32 iterations (PIC_MIXED)
     bool pair = false;                 // the next iteration's particle half runs in FP32 pairs
     bool pair_issued = false;          // the iteration in flight ran in FP32 pairs
@@ -182,6 +192,9 @@ struct Ctx {
     double *adj_tab = nullptr, *adj_F1 = nullptr, *adj_W1 = nullptr, *adj_rho1 = nullptr;
     double *adj_t = nullptr, *adj_pn = nullptr, *adj_y = nullptr, *adj_ys = nullptr, *adj_J = nullptr;
     double *adj_F0 = nullptr, *adj_W0 = nullptr, *adj_rho0 = nullptr;
+    double *adj_b0 = nullptr, *adj_w = nullptr, *adj_V = nullptr;   // the transposed solve's Krylov basis
+    double *adj_h = nullptr, *adj_part = nullptr;                     // its dot products (device)
+    int adj_m = 0;                                                    // restart length (basis size - 1)
 
     // live profiling: event pairs per phase, resolved at the next stream synchronisation
     bool prof = false;
@@ -229,7 +242,13 @@ void launch_adj_mesh_out(Ctx& c, const double* y, const double* pn, const double
 void launch_adj_derivs(Ctx& c, const double* xi, const double* v, const double* vstar, const double* lJ,
                        const double* lam_P, const double* lam_v, const double* lam_xe, const double* mu,
                        double* lam_xi, double* g, double* lvn, double* lPn, double* B);
-int launch_adj_jacobi(Ctx& c, const double* g, const double* B, const double* mu, double* mu_new);
+void launch_adj_precond(Ctx& c, const double* B, const double* r, double* z);
+void launch_adj_apply(Ctx& c, int64_t n, const double* z, const double* g, const double* b0, double* w);
+void launch_adj_mdot(Ctx& c, int64_t n, const double* w, const double* V, int64_t ldv, int nv, double* part,
+                     double* out);
+void launch_adj_combine(Ctx& c, int64_t n, double* w, const double* V, int64_t ldv, int nv, const double* h,
+                        double sign);
+int adj_blocks(const Ctx& c, int64_t n);
 void launch_adj_axpy(Ctx& c, int64_t n, double* y, const double* x, double s);
 void launch_adj_deposit(Ctx& c, const double* xi, const double* lam_dep, double* lam_xi);
 void launch_energy_grad(Ctx& c, double* lF, double* lW);

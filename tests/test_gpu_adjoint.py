@@ -10,14 +10,19 @@ Checks, from the smallest to the configured run:
 * the field energy after a few steps at 8^3, d W^N / d eps (perturbation amplitude) and
   d W^N / d v0 (beam speed), against the FP64 oracle's reference derivative (a Richardson-
   extrapolated central difference of the oracle's own steps, oracle/derivatives.py);
-* the configured adjoint run: 32^3, 16 particles per cell (524,288 electrons), 100 steps with
-  a checkpoint every 10, d W^N / d eps, d W^N / d v0 and a directional derivative along
-  the initial canonical momenta P^0, against central differences with h = 1e-6 of the GPU run.
+* the configured problem (32^3, 16 particles per cell, 524,288 electrons, a checkpoint every
+  10 steps) over 10 and 30 steps: d W^N / d eps, d W^N / d v0 and a directional derivative
+  along the initial canonical momenta P^0, against central differences of the GPU run with
+  h = 1e-8, where the quotients have converged in h;
+* the configured 100-step run: every step's transposed solve converges and the gradients do not
+  depend on the checkpoint schedule.
 
 The step map is only C0 where an orbit endpoint crosses a knot (the D_i A integrand and the
 point interpolant have kinks there, §4.3): a difference quotient whose interval holds such an
-event measures an average slope, not the derivative.  Over 100 steps of 524k particles some
-events fall inside the h = 1e-6 interval, which is what limits the agreement of the last check.
+event measures an average slope, not the derivative.  With 524k particles crossing knots every
+few steps, h = 1e-6 (a start moved by ~1e-5 cells) already holds such events within 10 steps,
+and past the two-stream saturation the run is chaotic, so no difference step checks the
+100-step gradient.
 """
 
 import numpy as np
@@ -201,27 +206,29 @@ def test_field_energy_gradient_matches_the_oracle_at_8c(sim, param):
     assert abs(got - ref) <= 1e-6 * abs(ref), (param, got, ref)
 
 
-def test_configured_adjoint_run_32c_100_steps(sim):
-    """32^3, 16 per cell (cold beams +-0.2, eps = 1e-3), 100 steps, checkpoints every 10:
-    d W^N / d eps, d W^N / d v0 and d W^N / dP^0 along a random direction u, against central
-    differences h = 1e-6 of the GPU forward run."""
-    import torch
+N32, PPB32, SEED32 = (32, 32, 32), 8, 1400
+
+
+def _gradients_32c(sim, torch, nsteps, every, direction_seed=11):
+    """The configured run's gradients (32^3, 16 per cell, cold beams +-0.2, eps = 1e-3):
+    d W^N / d eps, d W^N / d v0 and d W^N / d P^0 along a random direction u, with the sweeps
+    each step's transposed solve took.  Deterministic steps, so that a recomputed interval and
+    the difference quotients' runs repeat the forward run bit for bit.  The configuration fixes
+    no tolerance; tau = 1e-12 (at 1e-13 the run has a step whose iterations stall just above it)."""
     from paper_2606_15035_gb300 import adjoint
-    n, L, ppb, seed, nsteps = (32, 32, 32), pi.WORKLOADS["twostream-32c-2M"].L, 8, 1400, 100
+    L = pi.WORKLOADS["twostream-32c-2M"].L
     v0, eps = 0.2, 1e-3
-    xu, sign, q, m = _family(n, L, ppb, v0, eps, seed)
+    xu, sign, q, m = _family(N32, L, PPB32, v0, eps, SEED32)
     assert xu.shape[0] == 524288
-    # The configuration fixes no tolerance; tau = 1e-12 keeps the solves' noise in W^N near 1e-11
-    # of W, 1e-8 of the difference quotients' signal (W ~ eps^2, so 2 h / eps = 2e-3 of W); at
-    # 1e-13 the run has a step whose iterations stall just above it.
-    cfg = sim.pic_config_default(n=n, L=L, dt=0.1, picard_tol=1e-12, picard_max=64)
+    cfg = sim.pic_config_default(n=N32, L=L, dt=0.1, picard_tol=1e-12, picard_max=64, deterministic=1)
     e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
     b = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
     x0, P0 = _initial(torch, xu, sign, m, L, e, b)
     P0.retain_grad()
-    W = adjoint.field_energy_after(x0, P0, cfg, q, m, nsteps, every=10)
+    W = adjoint.field_energy_after(x0, P0, cfg, q, m, nsteps, every=every)
     W.backward()
-    u = torch.randn(P0.shape, generator=torch.Generator(device="cuda").manual_seed(11), device="cuda",
+    sweeps = list(W.grad_fn.vjp_iterations)
+    u = torch.randn(P0.shape, generator=torch.Generator(device="cuda").manual_seed(direction_seed), device="cuda",
                     dtype=torch.float64) * m * 1e-2
     got = {"eps": float(e.grad), "v0": float(b.grad), "P0.u": float((P0.grad * u).sum())}
 
@@ -235,9 +242,47 @@ def test_configured_adjoint_run_32c_100_steps(sim):
             s.close()
             return Wn
 
-    h = 1e-6
-    fd = {"eps": (W_of(eps + h, v0) - W_of(eps - h, v0)) / (2 * h),
-          "v0": (W_of(eps, v0 + h) - W_of(eps, v0 - h)) / (2 * h),
-          "P0.u": (W_of(eps, v0, h) - W_of(eps, v0, -h)) / (2 * h)}
+    def fd(h):
+        return {"eps": (W_of(eps + h, v0) - W_of(eps - h, v0)) / (2 * h),
+                "v0": (W_of(eps, v0 + h) - W_of(eps, v0 - h)) / (2 * h),
+                "P0.u": (W_of(eps, v0, h) - W_of(eps, v0, -h)) / (2 * h)}
+
+    return got, sweeps, fd
+
+
+@pytest.mark.parametrize("nsteps", [10, 30])
+def test_adjoint_matches_the_difference_limit_at_32c(sim, nsteps):
+    """The configured problem over 10 and 30 steps: the adjoint gradient against central
+    differences with h = 1e-8, inside the interval where the difference quotient has converged
+    in h.  Over 30 steps the run's 524k orbits cross about 1.5M knots; at h = 1e-6 some of those
+    crossings fall inside the difference interval (a particle's start moves by ~1e-5 cells), the
+    map's slope changes there, and the quotient is off the derivative by 1.3e-4 (10 steps) and
+    56% (30 steps); at h = 1e-7, 1e-8 and 1e-9 the quotients agree with each other and with the
+    adjoint to 2e-6 or better.  The checkpoint interval is 10 steps, as configured."""
+    import torch
+    got, sweeps, fd = _gradients_32c(sim, torch, nsteps, 10)
+    assert len(sweeps) == nsteps and max(sweeps) < 400
+    ref = fd(1e-8)
     for k in got:
-        assert abs(got[k] - fd[k]) <= 1e-4 * abs(fd[k]), (k, got[k], fd[k])
+        assert abs(got[k] - ref[k]) <= 1e-5 * abs(ref[k]), (nsteps, k, got[k], ref[k])
+
+
+def test_configured_adjoint_run_32c_100_steps(sim):
+    """The configured run: 32^3, 16 per cell (524,288 electrons), 100 steps, a checkpoint every
+    10 steps.  Every step's transposed solve converges, and the gradients equal those of the
+    same run checkpointed every 50 steps (another recompute schedule over the same deterministic
+    forward run).
+
+    Past the two-stream saturation (step ~60) the run is chaotic and its orbits cross knots
+    ~5M times in 100 steps: W^100 is not differentiable at the scale of any usable difference
+    step.  The central difference quotients of d W^100 / d eps at h = 1e-7, 1e-8 and 1e-9 are
+    -16.9, 147 and -392 (at 1e-6 a perturbed run has a step that does not converge), so they
+    cannot check the gradient there; the 10- and 30-step tests above check it where they can."""
+    import torch
+    got, sweeps, _ = _gradients_32c(sim, torch, 100, 10)
+    assert len(sweeps) == 100 and max(sweeps) < 400, sweeps
+    again, sweeps50, _ = _gradients_32c(sim, torch, 100, 50)
+    assert max(sweeps50) < 400
+    for k in got:
+        assert np.isfinite(got[k])
+        assert abs(got[k] - again[k]) <= 1e-6 * abs(again[k]), (k, got[k], again[k])
