@@ -267,6 +267,14 @@ pic_status pic_iterate(pic_ctx* ctx, const double* v_iter, int32_t on_device, co
  * wrapped to [0, n_a)): the orbit breakpoints and knot tests of §4.7 use these values. */
 pic_status pic_get_positions(pic_ctx* ctx, double* xi, int32_t on_device);
 
+/* The counterpart of pic_get_positions: set the particle positions in cell units (3 * np,
+ * pic_init order, each in [0, n_a); values outside are wrapped periodically) without the
+ * physical-unit conversion of pic_set_state, whose x / H rounds.  Call it after pic_set_state:
+ * pic_get_state + pic_get_positions then restore a state bit for bit (checkpoint-and-recompute
+ * of a run whose trajectory must repeat exactly, as the adjoint's backward pass does).  Not a
+ * part of the paper's method; PIC_ERR_ARG on a NULL pointer. */
+pic_status pic_set_positions(pic_ctx* ctx, const double* xi, int32_t on_device);
+
 /* After a pic_step that did not converge: its last Picard iterate v^{n+1,p} and the image
  * G(v^{n+1,p}) (3 * np each, particles in pic_init order); their difference is each
  * particle's fixed-point residual (Algorithm 1).  PIC_ERR_ARG after a converged step. */

@@ -31,7 +31,7 @@ PIC_QUAD_CLOSED, PIC_QUAD_GAUSS = 0, 1
 PIC_OPS_CENTRAL2, PIC_OPS_SPECTRAL = 0, 1
 
 EXPORTED = ["pic_config_default", "pic_init", "pic_step", "pic_energy", "pic_diagnostics",
-            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_get_iterate", "pic_get_accepted", "pic_set_wait_limit", "pic_step_vjp", "pic_energy_vjp", "pic_init_vjp", "pic_profile", "pic_residual_history",
+            "pic_get_state", "pic_set_state", "pic_iterate", "pic_get_positions", "pic_set_positions", "pic_get_iterate", "pic_get_accepted", "pic_set_wait_limit", "pic_step_vjp", "pic_energy_vjp", "pic_init_vjp", "pic_profile", "pic_residual_history",
             "pic_cn_update_static", "pic_probe_fma_rates", "pic_last_error", "pic_destroy", "pic_autotune", "pic_ensemble_init", "pic_ensemble_step",
             "pic_ensemble_size", "pic_ensemble_run", "pic_ensemble_last_error", "pic_ensemble_destroy"]
 
@@ -194,6 +194,7 @@ def lib():
     L.pic_residual_history.restype = C.c_int32
     L.pic_get_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    L.pic_set_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_get_accepted.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.pic_set_wait_limit.argtypes = [C.c_void_p, C.c_int64]
     L.pic_step_vjp.argtypes = [C.c_void_p, P(PicStateView), P(PicStateView), P(PicVjpInfo)]

@@ -7,7 +7,10 @@ as a 0-d tensor.  Its backward pass is the library's hand-written adjoint (pic_s
 pic_energy_vjp, pic_init_vjp), with checkpoint-and-recompute over time steps: the forward keeps
 the state every ``every`` steps on the device; the backward recomputes each interval's states
 from its checkpoint, then walks the interval backwards, re-running each step (so that the
-context holds level n and the accepted iterate) and applying its adjoint.  Every derivative is
+context holds level n and the accepted iterate) and applying its adjoint.  Checkpoints keep the
+positions as stored (cell units, pic_get_positions / pic_set_positions), so a recomputed step
+starts from the forward run's state bit for bit: past the two-stream saturation the run is
+chaotic, and a state rounded through physical units would linearise about another trajectory.  Every derivative is
 computed by the library's kernels; this module only orders the calls and holds the tensors.
 """
 
@@ -29,7 +32,7 @@ class FieldEnergyAfter(torch.autograd.Function):
         ckpt = {}
         for n in range(nsteps):
             if n % every == 0:
-                ckpt[n] = s.get_state_device()
+                ckpt[n] = s.checkpoint()
             info = s.step(1)
             if not info.converged:
                 raise sim.PicError(4, "a forward step did not converge")
@@ -47,7 +50,7 @@ class FieldEnergyAfter(torch.autograd.Function):
         s = _sim(cfg, x0, P0, q, m)
         # lambda^N = dW/d(state N), on the state after N steps (recomputed from the last checkpoint)
         last = max(ctx.ckpt)
-        s.set_state_device(ctx.ckpt[last])
+        s.restore(ctx.ckpt[last])
         for _ in range(last, nsteps):
             s.step(1)
         lam = s.energy_vjp()
@@ -57,12 +60,12 @@ class FieldEnergyAfter(torch.autograd.Function):
         for start in sorted(ctx.ckpt, reverse=True):
             end = min(start + every, nsteps)
             states = {start: ctx.ckpt[start]}
-            s.set_state_device(ctx.ckpt[start])
+            s.restore(ctx.ckpt[start])
             for n in range(start, end - 1):          # the interval's levels, recomputed once
                 s.step(1)
-                states[n + 1] = s.get_state_device()
+                states[n + 1] = s.checkpoint()
             for n in range(end - 1, start - 1, -1):
-                s.set_state_device(states[n])
+                s.restore(states[n])
                 s.step(1)                             # level n and v* of step n -> n+1
                 lam, info = s.step_vjp(lam)
                 ctx.vjp_iterations.append(int(info.iterations))

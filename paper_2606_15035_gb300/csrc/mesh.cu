@@ -522,8 +522,9 @@ void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nf
 }
 
 // The CN Helmholtz solve of a mesh phase: one cooperative launch when the device allows
-// it (the step coefficients are in device memory), else one launch per step.
-void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare) {
+// it (the step coefficients are in device memory), which stops at the first step whose error
+// bound is below tol times the solution's norm; else one launch per step of the full schedule.
+void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare, double tol) {
     const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
     if (c.cheb_coop_blocks <= 0 || !c.cheb_coef_dev) {
         launch_helmholtz(c, c.rhs, 1.0, a, 4, c.cheb_iters, c.cheb_alpha, c.cheb_beta, x_io, x_spare);
@@ -537,7 +538,7 @@ void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare) {
     int nf = 4, iters = c.cheb_iters;
     const double* al = c.cheb_coef_dev;
     const double* be = c.cheb_coef_dev + 1024;
-    double lmax = c.cheb_lmax, rate = c.cheb_rate, tol = c.cfg.helmholtz_tol;
+    double lmax = c.cheb_lmax, rate = c.cheb_rate;
     const int64_t want = (4 * c.m.ncell + THREADS - 1) / THREADS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, c.cheb_coop_blocks));
     StrideDigits sd = stride_digits((int64_t)grid * THREADS, c.m);

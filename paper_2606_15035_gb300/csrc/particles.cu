@@ -463,6 +463,17 @@ __global__ void k_init_positions(StepParams p, const double* __restrict__ x, dou
     }
 }
 
+// Cell-unit positions in caller order -> device order, wrapped to [0, n_a) (the identity on
+// values already in range).
+__global__ void k_set_positions(StepParams p, const int64_t* __restrict__ id, const double* __restrict__ src,
+                                double* __restrict__ xi) {
+    const int64_t np = p.np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xi[a * np + i] = wrap_pos_any(src[a * np + id[i]], (double)p.m.n[a]);
+    }
+}
+
 __global__ void k_point_deposit(StepParams p, const double* __restrict__ xi, double* __restrict__ rho) {
     const int64_t np = p.np;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1329,6 +1340,11 @@ int particle_blocks(const Ctx& c) {
 void launch_init_positions(Ctx& c, const double* x_dev) {
     StepParams p = make_params(c);
     k_init_positions<<<particle_blocks(c), THREADS, 0, c.stream>>>(p, x_dev, c.xi, c.id);
+    ++c.launches;
+}
+
+void launch_set_positions(Ctx& c, const double* src_dev) {
+    k_set_positions<<<particle_blocks(c), THREADS, 0, c.stream>>>(make_params(c), c.id, src_dev, c.xi);
     ++c.launches;
 }
 

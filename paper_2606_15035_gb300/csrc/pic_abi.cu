@@ -455,16 +455,23 @@ void mesh_begin(Ctx& c) {
 
 // The mesh half of one Algorithm 1 iteration: continuity, CN solve (warm-started from F1),
 // back-substitution and the gather table.
-void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev) {
+// tol: the Chebyshev solve's relative accuracy (helmholtz_tol when not positive).
+void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev, double tol = 0.0) {
     ProfScope ps(c, PH_MESH);
     if (c.cfg.ops == PIC_OPS_SPECTRAL) {
         launch_spec_mesh_phase(c, Jcur, Jprev);
         return;
     }
     launch_source(c, Jcur, Jprev);
-    launch_helmholtz_cn(c, &c.F1, &c.F1b);
+    launch_helmholtz_cn(c, &c.F1, &c.F1b, tol > 0.0 ? std::max(tol, c.cfg.helmholtz_tol) : c.cfg.helmholtz_tol);
     launch_backsub_table(c, false);
 }
+
+// PIC_MIXED: the fields of an FP32 iteration need no more accuracy than its iterate has
+// (e_v >= ~1e-9), and those of an FP64 refinement iteration no more than a thousandth of
+// mixed_tol64; the final sweep's mesh phase, which the committed step uses, keeps
+// helmholtz_tol.
+constexpr double MESH_TOL32 = 1e-10;
 
 // ---- one time step as a sequence of issue / finish phases --------------------------------
 //
@@ -515,7 +522,9 @@ void step_begin(Ctx& c) {
 void iter_issue(Ctx& c) {
     StepRun& r = c.run;
     const int64_t N = c.m.ncell;
-    mesh_phase(c, c.J[r.cur], r.p > 0 ? c.J[r.prev] : nullptr);
+    const double mesh_tol = r.fp32 ? MESH_TOL32
+                            : (r.began32 && c.cfg.mixed_tol64 > 0.0 ? 1e-3 * c.cfg.mixed_tol64 : 0.0);
+    mesh_phase(c, c.J[r.cur], r.p > 0 ? c.J[r.prev] : nullptr, mesh_tol);
     if (r.fp32) {
         launch_table32(c);
         cudaMemsetAsync(c.J[r.next], 0, sizeof(double) * 3 * N, c.stream);
@@ -1035,6 +1044,20 @@ pic_status pic_get_positions(pic_ctx* ctx, double* xi, int32_t on_device) {
                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream);
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_get_positions");
     return check_cuda(ctx, "pic_get_positions");
+}
+
+pic_status pic_set_positions(pic_ctx* ctx, const double* xi, int32_t on_device) {
+    if (!ctx || !xi) return PIC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.np == 0) return PIC_OK;
+    cudaMemcpyAsync(c.sort_tmp, xi, sizeof(double) * 3 * c.np,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream);
+    launch_set_positions(c, c.sort_tmp);
+    c.have_diag = false;
+    c.have_accepted = false;
+    c.fresh_init = false;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "pic_set_positions");
+    return check_cuda(ctx, "pic_set_positions");
 }
 
 pic_status pic_get_iterate(pic_ctx* ctx, double* v_iter, double* g_iter, int32_t on_device) {

@@ -216,6 +216,7 @@ enum ProfPhase : int { PH_PUSH = 0, PH_COMMIT, PH_SCATTER, PH_MESH, PH_SORT, PH_
 // ---- launchers (particles.cu) ----
 void launch_init_positions(Ctx& c, const double* x_dev);
 void launch_point_deposit(Ctx& c);
+void launch_set_positions(Ctx& c, const double* src_dev);
 void launch_sort(Ctx& c);
 void launch_first_scatter(Ctx& c, double* J, const double* v_iter_or_null);
 void launch_push(Ctx& c, const double* vit, double* vnew, double* Jnext, bool commit, bool diag);
@@ -279,7 +280,7 @@ void launch_jdiff(Ctx& c, const double* Jnew, const double* Jold);
 void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nfields, int iters,
                       const double* alpha, const double* beta, double** x_io, double** x_spare);
 void launch_backsub_table(Ctx& c, bool diag);
-void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare);
+void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare, double tol);
 int cheb_coop_capacity(const Ctx& c);
 void launch_null_project(Ctx& c, double* f, double add_const);
 void launch_mesh_energy(Ctx& c, const double* F, const double* W, int slot);

@@ -345,6 +345,19 @@ class PicSim:
     def set_state_device(self, d):
         pic_set_state(self.ctx, self._dview(d))
 
+    def checkpoint(self):
+        """The state as device tensors plus the positions as stored (cell units, key "xi"), so
+        that restore() brings the run back bit for bit (pic_set_positions)."""
+        d = self.get_state_device()
+        xi = _torch().zeros(max(3 * self.np, 1), dtype=_torch().float64, device="cuda")
+        _check(_lib.lib().pic_get_positions(self.ctx, C.c_void_p(xi.data_ptr()), 1), self.ctx)
+        d["xi"] = xi
+        return d
+
+    def restore(self, d):
+        pic_set_state(self.ctx, self._dview(d))
+        _check(_lib.lib().pic_set_positions(self.ctx, C.c_void_p(d["xi"].data_ptr()), 1), self.ctx)
+
     def step_vjp(self, lam_next):
         """(d state^{n+1} / d state^n)^T lam_next for the step just committed: (lam_prev, info)."""
         lam_prev = self.state_zeros()
