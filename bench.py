@@ -532,7 +532,7 @@ def main():
         pr = sm.profile(False)
         t_ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
         ev_h, ej_h, kind_h = sm.residual_history()
-        kinds = {0: "fp64", 1: "fp32", 2: "fp32-pair"}
+        kinds = {0: "fp64", 1: "fp32", 2: "fp32-pair", 3: "final-sweep residual of v*"}
         fin = lambda z: float(z) if np.isfinite(z) else None   # strict JSON: no Infinity
         history = [[fin(a), fin(b), kinds[int(k)]] for a, b, k in zip(ev_h, ej_h, kind_h)]
         return {"sim": sm, "prof": pr, "ms": t_ms, "drift": drift, "clocks": clk,

@@ -118,7 +118,13 @@ typedef struct {
                                      (m / 2) sum_i (v_i^{n+1} - v_i^n) . (G(v*)_i - v*_i) of the
                                      step's velocity change and the fixed-point residual (the
                                      orbit's power balance and the field-energy balance hold
-                                     exactly for the orbit of v*, §4.6, §4.8) */
+                                     exactly for the orbit of v*, §4.6, §4.8).  When this is > 0
+                                     and diagnostics are off, the first FP64 iterate v1 is also
+                                     tried as v* directly if its change times the FP32 phase's
+                                     contraction (e_v[1] / e_v[0]) is <= this: the final sweep
+                                     then measures v1's own residual ||G(v1) - v1|| / ||G(v1)||
+                                     and commits only if that is <= this (residual history kind
+                                     3); otherwise the FP64 iterations continue from v1 */
     int32_t mixed_pair_max;       /* PIC_MIXED: after the FP32 phase, at most this many refinement
                                      iterations whose particle half (orbit integrals, gather, push,
                                      next-orbit current) runs in FP32-pair arithmetic (two floats
@@ -353,7 +359,9 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable, pic_profile_t* out);
  * iteration k: ||v^{k+1} - v^k|| and the change of the orbit current between the two
  * iterates, relative; FP32 iterations record the previous update's current change, +inf at
  * the first) and fp32[k] = 1 if the iteration ran in FP32, 2 if its particle half ran in FP32
- * pairs (PIC_MIXED), else 0 (FP64).  Writes at
+ * pairs (PIC_MIXED), 3 for a final sweep that measured the residual ||G(v*) - v*|| / ||G(v*)||
+ * of its own iterate (PIC_MIXED, see mixed_tol64; e_J is then not measured, NaN), else 0
+ * (FP64).  Writes at
  * most `cap` entries into each non-NULL array and returns the number of iterations (which
  * may exceed cap), or -1 for a NULL context. */
 int32_t pic_residual_history(const pic_ctx* ctx, int32_t cap, double* e_v, double* e_J, int32_t* fp32);

@@ -724,6 +724,10 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
                     }
                     xi_out[a * np + i] = o.xe[a];
                     P_out[a * np + i] = o.Pw[a];
+                    // the residual of the accepted iterate itself, ||G(v*) - v*||
+                    const double d = o.vw[a] - vi[a];
+                    ev_num += d * d;
+                    ev_den += o.vw[a] * o.vw[a];
                 }
                 if constexpr (DIAG) {
                     double As[3], vb[3];
@@ -745,9 +749,9 @@ __global__ void __launch_bounds__(THREADS, DIAG ? 1 : 2) k_push(StepParams p, co
         }
         __syncthreads();   // order[] is rewritten by the next chunk
     }
+    write_partial<double>(partials, S_EV_NUM, ev_num, sm, false);
+    write_partial<double>(partials, S_EV_DEN, ev_den, sm, false);
     if constexpr (!COMMIT) {
-        write_partial<double>(partials, S_EV_NUM, ev_num, sm, false);
-        write_partial<double>(partials, S_EV_DEN, ev_den, sm, false);
         write_partial<double>(partials, S_PIECES_PUSH, pieces_push, sm, false);
         write_partial<double>(partials, S_PIECES_SCATTER, pieces_scatter, sm, false);
     } else if constexpr (DIAG) {

@@ -518,9 +518,27 @@ void step_begin(Ctx& c) {
     launch_finalize(c, S_JSCALE, 1, particle_blocks(c), false);
 }
 
+// The trial final sweep (PIC_MIXED, see iter_finish): the final sweep of v* = v^{p+1} with
+// the residual sums of v* itself; final_issue then has nothing left to queue if it passes.
+void trial_issue(Ctx& c) {
+    StepRun& r = c.run;
+    std::swap(c.vit, c.vnew);
+    mesh_phase(c, c.J[r.next], nullptr);
+    {
+        ProfScope ps(c, PH_COMMIT);
+        launch_push(c, c.vit, c.vnew, nullptr, true, false);
+    }
+    launch_finalize(c, S_EV_NUM, 2, particle_blocks(c), false);
+    queue_results(c);
+}
+
 // Queue iteration r.p and the copy of its residual sums.
 void iter_issue(Ctx& c) {
     StepRun& r = c.run;
+    if (r.trial) {
+        trial_issue(c);
+        return;
+    }
     const int64_t N = c.m.ncell;
     const double mesh_tol = r.fp32 ? MESH_TOL32
                             : (r.began32 && c.cfg.mixed_tol64 > 0.0 ? 1e-3 * c.cfg.mixed_tol64 : 0.0);
@@ -571,6 +589,36 @@ pic_status iter_finish(pic_ctx* ctx) {
     StepRun& r = c.run;
     const int64_t N = c.m.ncell;
     const double* h = c.host_results;
+    if (r.trial) {
+        // the trial final sweep of v* = v^{p+1}: its own residual ||G(v*) - v*|| / ||G(v*)||
+        r.trial = false;
+        const double num = h[S_EV_NUM], den = h[S_EV_DEN];
+        const double res = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        c.hist_ev.push_back(res);
+        c.hist_eJ.push_back(NAN);
+        c.hist_fp32.push_back(3);
+        if (!std::isfinite(res)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite residual of the final sweep");
+        if (res <= c.cfg.mixed_tol64) {
+            r.e_v = res;
+            r.converged = true;
+            r.iterating = false;
+            r.final_done = true;
+            r.after32 = false;
+            return PIC_OK;
+        }
+        // rejected: the FP64 iterations continue from v^{p+1} (now in vit) as after any
+        // iteration; the sweep's mesh fields are those of J(v^{p+1}), the next one's warm start
+        ++r.p64;
+        r.after32 = false;
+        r.hist = r.p64 >= 2;
+        r.rotate();
+        if (r.p == c.cfg.picard_max) {
+            r.iterating = false;
+            return PIC_OK;
+        }
+        ++r.p;
+        return PIC_OK;
+    }
     if (r.p == 0) r.jscale = std::sqrt((double)N) * std::fabs(c.q) * h[S_JSCALE] / c.volume;
     {
         // FP64 iterations: the change of the orbit current made by this update, J(v^{p+1})
@@ -591,6 +639,8 @@ pic_status iter_finish(pic_ctx* ctx) {
         c.hist_fp32.push_back(1);
         if (!std::isfinite(r.e_v)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite FP32 residual");
         ++r.p32;
+        if (r.p32 == 1) r.e_v32_first = r.e_v;
+        else if (r.p32 == 2 && r.e_v32_first > 0.0) r.rho32 = r.e_v / r.e_v32_first;
         // the FP32 iterations' e_J measures the change that iteration p - 1 made to v, so e_v
         // alone says that the FP32 iterate has reached the FP32 noise floor
         const bool reached = r.e_v <= c.cfg.mixed_tol32;
@@ -654,6 +704,14 @@ pic_status iter_finish(pic_ctx* ctx) {
             r.iterating = false;
             return PIC_OK;
         }
+        // PIC_MIXED: the first FP64 iterate v^{p+1} is tried as v* when its change times the
+        // FP32 phase's contraction predicts a residual within mixed_tol64; the final sweep of
+        // the trial measures that residual and commits only if it is within (trial_issue)
+        if (!r.pair_issued && r.after32 && c.cfg.mixed_tol64 > 0.0 && !c.cfg.diagnostics && r.rho32 > 0.0 &&
+            r.rho32 < 1.0 && r.e_v * r.rho32 <= c.cfg.mixed_tol64) {
+            r.trial = true;
+            return PIC_OK;
+        }
         if (r.p == c.cfg.picard_max) {
             r.iterating = false;
             return PIC_OK;
@@ -701,6 +759,10 @@ pic_status iter_close(pic_ctx* ctx, pic_step_info* last) {
 // Final consistency sweep (§5.4): orbit of v^{n+1,p+1}, whose current is in J[next].
 void final_issue(Ctx& c) {
     const StepRun& r = c.run;
+    if (r.final_done) {   // the trial final sweep already ran and passed
+        queue_results(c);
+        return;
+    }
     const bool diag = c.cfg.diagnostics != 0;
     std::swap(c.vit, c.vnew);
     double* Jfin = c.J[r.next];

@@ -85,6 +85,10 @@ struct StepRun {
     bool fp32 = false;                 // the next iteration runs in FP32 (PIC_MIXED)
     bool hist = false;                 // vnew holds the previous iterate v^{p-1}
     bool after32 = false;              // the iteration in flight is the first FP64 one after FP32
+    bool trial = false;                // the next issue is a final sweep of v^{p+1} that measures
+                                       // its residual (PIC_MIXED), instead of an iteration
+    bool final_done = false;           // that sweep was accepted: the step only needs its commit
+    double e_v32_first = 0.0, rho32 = 0.0;   // FP32 phase: first e_v, contraction e_v[1] / e_v[0]
     bool began32 = false;              // the step began with FP32 iterations (PIC_MIXED)
     bool pair = false;                 // the next iteration's particle half runs in FP32 pairs
     bool pair_issued = false;          // the iteration in flight ran in FP32 pairs

@@ -139,6 +139,33 @@ def test_c1_run_is_a_fixed_point_of_algorithm1_every_step(sim, accel, precision)
     s.close()
 
 
+def test_mixed_verified_acceptance_is_a_fixed_point(sim):
+    """The mixed path with mixed_tol64 = 1e-10 tries its first FP64 iterate as v*: the final
+    sweep measures ||G(v*) - v*|| / ||G(v*)|| itself (residual history kind 3) and commits only
+    within 1e-10, else the FP64 iterations go on.  Every step, however it ended, is checked as
+    above with 1e-10 in place of tau: the committed level is the oracle's body at v*, v* is a
+    fixed point to 2e-10 and the current error is within 2e-10; a step accepted by the sweep
+    also reports the residual the oracle finds."""
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.workload_particles(w)
+    tol = 1e-10
+    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, precision=1, mixed_tol64=tol,
+                   picard_max=w.picard_max)
+    swept = 0
+    for k in range(20):
+        o_n = oracle_level(s, q, m)
+        res, _ = check_accepted_step(s, o_n, ocfg, tol)
+        ev, ej, kind = s.residual_history()
+        if kind[-1] == 3:
+            swept += 1
+            assert ev[-1] <= tol and np.isnan(ej[-1])
+            assert abs(ev[-1] - res) <= 1e-2 * res + 1e-15, (k, ev[-1], res)
+        else:
+            assert (kind == 3).sum() <= 1 and ev[-1] <= tol
+    assert swept >= 1
+    s.close()
+
+
 @pytest.mark.parametrize("kind", ["spectral", "r2", "r3", "ragged"])
 def test_other_paths_are_fixed_points(sim, kind):
     """The spectral operators, the degree-2 and -3 shapes (split Gauss rule) and a ragged mesh
