@@ -47,7 +47,7 @@ MIXED_TOL64 = 1e-10       # FP64 refinement tolerance of the mixed path (energy 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 SUB_CELLS = 16            # the CPU oracle's sample: a periodic sub-box of SUB_CELLS^3 cells
-CPU_STEPS = 3             # timed oracle steps of the cpu_baseline leg
+CPU_STEPS = 10            # timed oracle steps of the cpu_baseline leg
 
 # Algorithmic FP64 flops (add, mul = 1, FMA = 2; the scatter's atomic adds counted) of the
 # fused push + next-orbit scatter kernel, counted from the kernel source per particle and per

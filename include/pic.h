@@ -89,7 +89,10 @@ typedef struct {
     double helmholtz_tol;         /* accuracy of the CN Helmholtz solve (Chebyshev, central2): each
                                      mesh phase runs the fewest steps whose error bound is below
                                      helmholtz_tol times the solution's norm, from the warm start's
-                                     residual (at most the schedule that reduces any start by it) */
+                                     residual (at most the schedule that reduces any start by it).
+                                     On a mesh whose sizes are all 2^p 3^q <= 1024 the central2
+                                     solve is by FFT instead, exact per mode (the wide Laplacian's
+                                     symbol), and this does not apply to it */
     double mixed_tol32;           /* PIC_MIXED: leave the FP32 iterations once e_v <= this */
     int32_t mixed_max32;          /* PIC_MIXED: at most this many FP32 iterations per step */
     int32_t deterministic;        /* 1: bitwise reproducible steps.  The particle sort is a stable
@@ -119,12 +122,14 @@ typedef struct {
                                      step's velocity change and the fixed-point residual (the
                                      orbit's power balance and the field-energy balance hold
                                      exactly for the orbit of v*, §4.6, §4.8).  When this is > 0
-                                     and diagnostics are off, the first FP64 iterate v1 is also
-                                     tried as v* directly if its change times the FP32 phase's
-                                     contraction (e_v[1] / e_v[0]) is <= this: the final sweep
-                                     then measures v1's own residual ||G(v1) - v1|| / ||G(v1)||
-                                     and commits only if that is <= this (residual history kind
-                                     3); otherwise the FP64 iterations continue from v1 */
+                                     and diagnostics are off, an FP64 iterate v^{p+1} is also
+                                     tried as v* directly once its residual is predicted <= this
+                                     (from the ratio of residual to current change e_J that earlier
+                                     trials measured, else from the contraction of the iterations
+                                     so far): the final sweep then measures its own residual
+                                     ||G(v*) - v*|| / ||G(v*)|| and commits only if that is <= this
+                                     (residual history kind 3); otherwise the FP64 iterations
+                                     continue from v^{p+1} */
     int32_t mixed_pair_max;       /* PIC_MIXED: after the FP32 phase, at most this many refinement
                                      iterations whose particle half (orbit integrals, gather, push,
                                      next-orbit current) runs in FP32-pair arithmetic (two floats
@@ -232,6 +237,11 @@ typedef struct {
                                     tile, so that they gathered and scattered in global memory */
     int64_t pushpair_launches;   /* FP32-pair push + scatter launches (PIC_MIXED refinement) */
     double pushpair_ms;          /* their summed event durations */
+    int64_t local_failed;        /* local solves whose best residual stayed above 1e-10 of the
+                                    particle's speed (their pinned components aside, the residual
+                                    stays in the committed step as an energy defect) */
+    int64_t local_failed_unpinned; /* ... of them with no component within 1e-6 cells of a knot,
+                                    so none was pinned */
 } pic_profile_t;
 
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,

@@ -165,6 +165,8 @@ class PicProfile(C.Structure):
         ("push32_chunks_global", C.c_int64),
         ("pushpair_launches", C.c_int64),
         ("pushpair_ms", C.c_double),
+        ("local_failed", C.c_int64),
+        ("local_failed_unpinned", C.c_int64),
     ]
 
 

@@ -483,6 +483,10 @@ __global__ void k_scale_copy(double* __restrict__ dst, const double* __restrict_
     GRID_LOOP(i, n) dst[i] = s * src[i];
 }
 
+__global__ void k_add_to(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+    GRID_LOOP(i, n) dst[i] += src[i];
+}
+
 }  // namespace
 
 int mesh_blocks(const Ctx& c) {
@@ -519,6 +523,26 @@ void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nf
         ++c.launches;
         std::swap(*x_io, *x_spare);
     }
+}
+
+// The CN Helmholtz solve of a mesh phase by FFT (c.helm_fft), exact per mode up to the
+// transforms' rounding (~1e-14 of the solution), then one step of iterative refinement: the
+// residual r = b - (I - a Delta_h) x from the stencil (a k_cheb step with alpha = 0, beta = 1
+// leaves r in c.cheb_d), its FFT solve, x += that.  The refined solution is accurate to the
+// rounding of the residual, like the Chebyshev solve at helmholtz_tol; psi and U, which take
+// 2 / dt times the change of phi and A, need that.
+void launch_helmholtz_fft_refined(Ctx& c, double* x) {
+    const double a = 0.25 * c.cfg.kappa * c.cfg.kappa * c.cfg.dt * c.cfg.dt;
+    const int64_t N = c.m.ncell;
+    launch_helmholtz_fft(c, c.rhs, x, 4, a);
+    MeshParams p = mesh_params(c);
+    dim3 grid(mesh_blocks(c), 4);
+    const StrideDigits sd = stride_digits((int64_t)grid.x * THREADS, c.m);
+    k_cheb<<<grid, THREADS, 0, c.stream>>>(p, x, c.F1b, c.cheb_d, c.rhs, 1.0, a, 0.0, 1.0, sd);
+    ++c.launches;
+    launch_helmholtz_fft(c, c.cheb_d, c.F1b, 4, a);
+    k_add_to<<<mesh_blocks(c), THREADS, 0, c.stream>>>(x, c.F1b, 4 * N);
+    ++c.launches;
 }
 
 // The CN Helmholtz solve of a mesh phase: one cooperative launch when the device allows

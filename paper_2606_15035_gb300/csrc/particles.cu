@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
     bool brk[3], secok[3], sl[3], probe[3];
     int nrep[3];
     double tol = 0.0, spd = 0.0, gm = 0.0, brs = 0.0;
-    double nsolve = 0.0, neval = 0.0;
+    double nsolve = 0.0, neval = 0.0, nfail = 0.0, nfail_free = 0.0;
     while (true) {
         if (!active && !exhausted) {
             int64_t k = -1;
@@ -1063,9 +1063,14 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
         // itself costs less.
         {
             const bool failed = brs > FAIL_RES * spd;
+            bool pinned = false;
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+            for (int a = 0; a < 3; ++a) {
                 if ((brs > tol && bu[a] == uland[a]) || (failed && fabs(dk[a]) < D_FALLBACK)) sl[a] = true;
+                pinned = pinned || (failed && fabs(dk[a]) < D_FALLBACK);
+            }
+            nfail += failed ? 1.0 : 0.0;
+            nfail_free += (failed && !pinned) ? 1.0 : 0.0;
         }
         uint8_t sb = 0;
 #pragma unroll
@@ -1095,6 +1100,8 @@ __global__ void __launch_bounds__(THREADS) k_local(StepParams p, const double* _
     write_partial<double>(partials, S_EVL_DEN, ev_den, sm, false);
     write_partial<double>(partials, S_LOCAL_SOLVES, nsolve, sm, false);
     write_partial<double>(partials, S_LOCAL_EVALS, neval, sm, false);
+    write_partial<double>(partials, S_LOCAL_FAILED, nfail, sm, false);
+    write_partial<double>(partials, S_LOCAL_FAILED_FREE, nfail_free, sm, false);
 }
 
 __global__ void k_kinetic(StepParams p, const double* __restrict__ v, double* __restrict__ partials) {

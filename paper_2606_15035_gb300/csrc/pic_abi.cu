@@ -345,12 +345,35 @@ pic_status allocate(pic_ctx* ctx) {
         c.inv_u_J = inv_u(wq * 100.0 * c.cfg.kappa);
         c.inv_u_rho = inv_u(wq);
     }
+    // central differences on a mesh the FFT takes: the CN Helmholtz solves go through it
+    if (c.cfg.ops == PIC_OPS_CENTRAL2) {
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            int radix[FFT_MAX_STAGES], nst = 0;
+            ok = ok && fft_factor(c.m.n[a], radix, nst);
+        }
+        c.helm_fft = ok;
+    }
+    if (c.helm_fft) {
+        ALLOC(c.helm_spec, double2, 4 * N);
+        ALLOC(c.helm_s2, double, c.m.n[0] + c.m.n[1] + c.m.n[2]);
+        std::vector<double> s2;
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < c.m.n[a]; ++i) {
+                const double sn = std::sin(2.0 * M_PI * i / c.m.n[a]);
+                s2.push_back(sn * sn * c.invH[a] * c.invH[a]);
+            }
+        cudaMemcpyAsync(c.helm_s2, s2.data(), sizeof(double) * s2.size(), cudaMemcpyHostToDevice, c.stream);
+        if (cudaStreamSynchronize(c.stream) != cudaSuccess) return check_cuda(ctx, "helmholtz symbols");
+    }
     if (c.cfg.ops == PIC_OPS_SPECTRAL) {
         ALLOC(c.spec0, double2, 9 * N);
         ALLOC(c.spec1, double2, 12 * N);
         ALLOC(c.specJ, double2, 3 * N);
         ALLOC(c.specR, double2, 3 * N);
         ALLOC(c.spec_gphi, double, 3 * N);
+    }
+    if (c.cfg.ops == PIC_OPS_SPECTRAL || c.helm_fft) {
         for (int a = 0; a < 3; ++a) {
             fft_factor(c.m.n[a], c.fft_radix[a], c.fft_nst[a]);
             std::vector<double2> tw;
@@ -463,7 +486,11 @@ void mesh_phase(Ctx& c, const double* Jcur, const double* Jprev, double tol = 0.
         return;
     }
     launch_source(c, Jcur, Jprev);
-    launch_helmholtz_cn(c, &c.F1, &c.F1b, tol > 0.0 ? std::max(tol, c.cfg.helmholtz_tol) : c.cfg.helmholtz_tol);
+    if (c.helm_fft) {
+        launch_helmholtz_fft_refined(c, c.F1);   // to roundoff: the tolerance does not apply
+    } else {
+        launch_helmholtz_cn(c, &c.F1, &c.F1b, tol > 0.0 ? std::max(tol, c.cfg.helmholtz_tol) : c.cfg.helmholtz_tol);
+    }
     launch_backsub_table(c, false);
 }
 
@@ -575,7 +602,7 @@ void iter_issue(Ctx& c) {
         if (c.cfg.picard_accel) launch_finalize(c, S_EVL_NUM, 2, local_blocks(c), false);
         launch_finalize(c, S_EJ_NUM, 2, mesh_blocks(c), false);
         if (c.prof) launch_finalize(c, S_PIECES_PUSH, 2, particle_blocks(c), false);
-        if (c.prof && c.cfg.picard_accel) launch_finalize(c, S_LOCAL_SOLVES, 2, local_blocks(c), false);
+        if (c.prof && c.cfg.picard_accel) launch_finalize(c, S_LOCAL_SOLVES, 4, local_blocks(c), false);
         c.last_v = c.vit;
         c.last_g = c.vnew;
     }
@@ -598,6 +625,10 @@ pic_status iter_finish(pic_ctx* ctx) {
         c.hist_eJ.push_back(NAN);
         c.hist_fp32.push_back(3);
         if (!std::isfinite(res)) return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite residual of the final sweep");
+        // the measured ratio of residual to current change, for the next predictions (a larger
+        // one at once, a smaller one halfway, so that one quiet step does not license the next)
+        if (r.trial_eJ > 0.0 && std::isfinite(r.trial_eJ))
+            c.trial_kappa = std::max(res / r.trial_eJ, 0.5 * c.trial_kappa);
         if (res <= c.cfg.mixed_tol64) {
             r.e_v = res;
             r.converged = true;
@@ -608,9 +639,10 @@ pic_status iter_finish(pic_ctx* ctx) {
         }
         // rejected: the FP64 iterations continue from v^{p+1} (now in vit) as after any
         // iteration; the sweep's mesh fields are those of J(v^{p+1}), the next one's warm start
+        r.e_v64_prev = r.e_v;
         ++r.p64;
         r.after32 = false;
-        r.hist = r.p64 >= 2;
+        r.hist = r.p64 >= (r.began32 ? 2 : 1);
         r.rotate();
         if (r.p == c.cfg.picard_max) {
             r.iterating = false;
@@ -673,6 +705,8 @@ pic_status iter_finish(pic_ctx* ctx) {
             if (c.cfg.picard_accel) {
                 c.prof_acc.local_solves += (int64_t)h[S_LOCAL_SOLVES];
                 c.prof_acc.local_evals += (int64_t)h[S_LOCAL_EVALS];
+                c.prof_acc.local_failed += (int64_t)h[S_LOCAL_FAILED];
+                c.prof_acc.local_failed_unpinned += (int64_t)h[S_LOCAL_FAILED_FREE];
             }
         }
         double num = h[S_EV_NUM], den = h[S_EV_DEN];
@@ -704,14 +738,28 @@ pic_status iter_finish(pic_ctx* ctx) {
             r.iterating = false;
             return PIC_OK;
         }
-        // PIC_MIXED: the first FP64 iterate v^{p+1} is tried as v* when its change times the
-        // FP32 phase's contraction predicts a residual within mixed_tol64; the final sweep of
-        // the trial measures that residual and commits only if it is within (trial_issue)
-        if (!r.pair_issued && r.after32 && c.cfg.mixed_tol64 > 0.0 && !c.cfg.diagnostics && r.rho32 > 0.0 &&
-            r.rho32 < 1.0 && r.e_v * r.rho32 <= c.cfg.mixed_tol64) {
-            r.trial = true;
-            return PIC_OK;
+        // PIC_MIXED: the FP64 iterate v^{p+1} is tried as v* when its predicted residual is
+        // within mixed_tol64; the final sweep of the trial measures that residual and commits
+        // only if it is within (trial_issue).  The prediction: the residual left by an update is
+        // driven by the change of the current it made, so once a trial has measured the ratio
+        // kappa = ||G(v*) - v*|| / e_J, 2 kappa e_J; before that, the contraction seen so far
+        // (the FP32 phase's e_v[1] / e_v[0] after the first FP64 iteration, else the last two
+        // FP64 e_v) times e_v.
+        if (!r.pair_issued && r.began32 && c.cfg.mixed_tol64 > 0.0 && !c.cfg.diagnostics) {
+            double pred = INFINITY;
+            if (c.trial_kappa > 0.0 && std::isfinite(r.e_J)) {
+                pred = 2.0 * c.trial_kappa * r.e_J;
+            } else {
+                const double rho = r.after32 ? r.rho32 : (r.e_v64_prev > 0.0 ? r.e_v / r.e_v64_prev : 0.0);
+                if (rho > 0.0 && rho < 1.0) pred = rho * r.e_v;
+            }
+            if (pred <= c.cfg.mixed_tol64) {
+                r.trial = true;
+                r.trial_eJ = r.e_J;
+                return PIC_OK;
+            }
         }
+        r.e_v64_prev = r.e_v;
         if (r.p == c.cfg.picard_max) {
             r.iterating = false;
             return PIC_OK;

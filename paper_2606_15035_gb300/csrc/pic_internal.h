@@ -42,6 +42,8 @@ enum Slot : int {
     S_PIECES_SCATTER,  // orbit pieces visited by the scatter of the next orbit (profiling)
     S_LOCAL_SOLVES,    // particle-local solves made by k_local (profiling)
     S_LOCAL_EVALS,     // push evaluations made by those solves (profiling)
+    S_LOCAL_FAILED,    // solves that ended above FAIL_RES of the speed (profiling)
+    S_LOCAL_FAILED_FREE,  // ... of them with no component pinned to a knot (profiling)
     S_CHUNKS32,        // particle chunks pushed by the FP32 push (profiling)
     S_CHUNKS32_GLOBAL, // ... of which gathered and scattered through global memory (box too big)
     S_PROJ0,       // 8 null-mode projections (init)
@@ -89,6 +91,8 @@ struct StepRun {
                                        // its residual (PIC_MIXED), instead of an iteration
     bool final_done = false;           // that sweep was accepted: the step only needs its commit
     double e_v32_first = 0.0, rho32 = 0.0;   // FP32 phase: first e_v, contraction e_v[1] / e_v[0]
+    double e_v64_prev = 0.0;           // e_v of the previous FP64 iteration
+    double trial_eJ = 0.0;             // e_J of the iteration whose iterate the trial sweeps
     bool began32 = false;              // the step began with FP32 iterations (PIC_MIXED)
     bool pair = false;                 // the next iteration's particle half runs in FP32 pairs
     bool pair_issued = false;          // the iteration in flight ran in FP32 pairs
@@ -150,6 +154,7 @@ struct Ctx {
     std::vector<double> hist_ev, hist_eJ;   // residuals of the last step's iterations
     std::vector<int32_t> hist_fp32;
     StepRun run;
+    double trial_kappa = 0.0;          // PIC_MIXED: measured ||G(v*) - v*|| / e_J of trial sweeps
     // spectral operators (ops = PIC_OPS_SPECTRAL): transforms of level n [phi, A | psi, U | rho]
     // (9 N), of level n+1 and D phi^{n+1/2} (12 N), of J (3 N), residual scratch (3 N), the
     // real D phi^{n+1/2} (3 N), and the FFT plan of each axis
@@ -158,6 +163,11 @@ struct Ctx {
     double2* fft_tw[3] = {nullptr, nullptr, nullptr};
     int fft_radix[3][FFT_MAX_STAGES] = {};
     int fft_nst[3] = {0, 0, 0};
+    // central-difference operators on a 2^p 3^q mesh: the CN Helmholtz solve of each mesh phase
+    // by FFT (4 N complex scratch, per-axis symbols sin^2(2 pi m / n_a) / H_a^2)
+    bool helm_fft = false;
+    double2* helm_spec = nullptr;
+    double* helm_s2 = nullptr;
     // deterministic mode: exact deposit accumulators (3 N each), their scales, creeping flags,
     // and the radix-sort work arrays
     long long *acc_hi = nullptr, *acc_lo = nullptr;
@@ -271,6 +281,7 @@ void launch_spec_mesh_phase(Ctx& c, const double* Jcur, const double* Jprev);
 void launch_spec_energy(Ctx& c, const double* F, const double* W, int slot);
 void launch_spec_diag(Ctx& c, const double* Jfinal);
 void launch_spec_poisson(Ctx& c);
+void launch_helmholtz_fft(Ctx& c, const double* b, double* x, int nf, double a);
 int radix_tiles(int64_t np);
 int push32_blocks(const Ctx& c);   // grid of the FP32 chunk kernels (partials per block)
 void launch_table32(Ctx& c);
@@ -285,6 +296,7 @@ void launch_helmholtz(Ctx& c, const double* b, double c_id, double c_lap, int nf
                       const double* alpha, const double* beta, double** x_io, double** x_spare);
 void launch_backsub_table(Ctx& c, bool diag);
 void launch_helmholtz_cn(Ctx& c, double** x_io, double** x_spare, double tol);
+void launch_helmholtz_fft_refined(Ctx& c, double* x);
 int cheb_coop_capacity(const Ctx& c);
 void launch_null_project(Ctx& c, double* f, double add_const);
 void launch_mesh_energy(Ctx& c, const double* F, const double* W, int slot);

@@ -167,6 +167,25 @@ __global__ void k_spec_cn(SpecParams p, const double2* __restrict__ Jh, const do
     }
 }
 
+// The CN Helmholtz solve of the central-difference operators by FFT: (I - a Delta_h) x = b, the
+// wide Laplacian sum_a (f_{+2} - 2 f + f_{-2}) / (4 H_a^2) having the symbol -sum_a s2_a[m_a],
+// s2_a[m] = sin^2(2 pi m / n_a) / H_a^2, so each mode is divided by 1 + a sum_a s2_a[m_a] (>= 1;
+// the 1/N of the inverse transform is folded in).
+__global__ void k_helm_fft_divide(MeshDims m, const double* __restrict__ s2, double a, double invN,
+                                  double2* __restrict__ data, int nf) {
+    const int64_t N = m.ncell;
+    SPEC_LOOP(g, N) {
+        const int ix = (int)(g % m.n[0]);
+        const int64_t t = g / m.n[0];
+        const int iy = (int)(t % m.n[1]), iz = (int)(t / m.n[1]);
+        const double d = invN / (1.0 + a * (s2[ix] + s2[m.n[0] + iy] + s2[m.n[0] + m.n[1] + iz]));
+        for (int f = 0; f < nf; ++f) {
+            const double2 z = data[f * N + g];
+            data[f * N + g] = make_double2(z.x * d, z.y * d);
+        }
+    }
+}
+
 // Gather table per node: A^n (3), A^{n+1} (3), D phi^{n+1/2} (3), U^{n+1/2} (3).
 __global__ void k_spec_table(int64_t N, const double* __restrict__ F0, const double* __restrict__ W0,
                              const double* __restrict__ F1, const double* __restrict__ W1,
@@ -429,6 +448,19 @@ void launch_spec_diag(Ctx& c, const double* Jfinal) {
     fft3(c, c.specR, 3, true);
     k_spec_diag<<<mesh_blocks(c), THREADS, 0, c.stream>>>(p, Jfinal, c.spec_gphi, c.W0, c.W1, c.specR, c.partials);
     ++c.launches;
+}
+
+// (I - a Delta_h) x = b for nf fields with the central-difference Laplacian, exactly per mode
+// (c.helm_spec: nf N complex scratch; c.helm_s2: the per-axis symbols).
+void launch_helmholtz_fft(Ctx& c, const double* b, double* x, int nf, double a) {
+    const int64_t N = c.m.ncell;
+    r2c(c, b, c.helm_spec, nf * N);
+    fft3(c, c.helm_spec, nf, false);
+    k_helm_fft_divide<<<spec_blocks(c, N), THREADS, 0, c.stream>>>(c.m, c.helm_s2, a, 1.0 / (double)N, c.helm_spec,
+                                                                   nf);
+    ++c.launches;
+    fft3(c, c.helm_spec, nf, true);
+    c2r(c, c.helm_spec, x, nf * N, 1.0);
 }
 
 // Initial potential: -Delta_h phi = sigma1 rho, zero on the null modes (§5.4).

@@ -140,9 +140,9 @@ def test_c1_run_is_a_fixed_point_of_algorithm1_every_step(sim, accel, precision)
 
 
 def test_mixed_verified_acceptance_is_a_fixed_point(sim):
-    """The mixed path with mixed_tol64 = 1e-10 tries its first FP64 iterate as v*: the final
-    sweep measures ||G(v*) - v*|| / ||G(v*)|| itself (residual history kind 3) and commits only
-    within 1e-10, else the FP64 iterations go on.  Every step, however it ended, is checked as
+    """The mixed path with mixed_tol64 = 1e-10 tries an FP64 iterate as v* once its residual is
+    predicted within 1e-10: the final sweep measures ||G(v*) - v*|| / ||G(v*)|| itself (residual
+    history kind 3) and commits only within 1e-10, else the FP64 iterations go on.  Every step, however it ended, is checked as
     above with 1e-10 in place of tau: the committed level is the oracle's body at v*, v* is a
     fixed point to 2e-10 and the current error is within 2e-10; a step accepted by the sweep
     also reports the residual the oracle finds."""
@@ -156,12 +156,15 @@ def test_mixed_verified_acceptance_is_a_fixed_point(sim):
         o_n = oracle_level(s, q, m)
         res, _ = check_accepted_step(s, o_n, ocfg, tol)
         ev, ej, kind = s.residual_history()
+        tried = np.flatnonzero(kind == 3)
         if kind[-1] == 3:
             swept += 1
             assert ev[-1] <= tol and np.isnan(ej[-1])
             assert abs(ev[-1] - res) <= 1e-2 * res + 1e-15, (k, ev[-1], res)
+            tried = tried[:-1]
         else:
-            assert (kind == 3).sum() <= 1 and ev[-1] <= tol
+            assert ev[-1] <= tol
+        assert (ev[tried] > tol).all()          # a sweep that did not commit found its iterate short
     assert swept >= 1
     s.close()
 
@@ -208,6 +211,33 @@ def test_near_knot_states_are_fixed_points_or_slide(sim, seed, far, amp):
     st.phi, st.psi, st.A, st.U, st.rho = o.phi, o.psi, o.A, o.U, o.rho
     s.set_state(st)
     check_accepted_step(s, oracle_level(s, o.q, o.m), ocfg, ocfg.picard_tol)
+    s.close()
+
+
+def test_late_time_thermal_8c_steps_are_fixed_points(sim):
+    """Past the two-stream saturation: the 8^3 thermal workload (8 per beam per cell, beams
+    +-0.2, eps = 1e-3, thermal spread 1e-4) run for 85 steps on the GPU, where orbits creep
+    across y and z knots under strong D_i A forces and the loop needs 2-3 times the early
+    iterations per step.  The energy stays at roundoff over the run, and the next two steps are
+    checked against the oracle's map at the GPU's accepted iterate.  (From step ~90 on, some
+    particle-local solves of this run end above 1e-10 of their speed, and from step ~105 a
+    near-knot one is pinned to its knot now and then, each such step moving the energy by
+    ~1e-11: the limit the 32^3 run meets sooner, measured per step by pic_profile's
+    local_failed counters.)"""
+    n, L = (8, 8, 8), pi.WORKLOADS["twostream-8c-8k"].L
+    x, v, q, m = pi.random_twostream(n, L, 8, 0.2, 1e-3, 1e-4, 1140)
+    s, ocfg = make(sim, x, v, q, m, n, L, 1e-13, picard_max=40)
+    e0 = s.energy().total
+    drift, iters = 0.0, []
+    for _ in range(85):
+        info = s.step(1)
+        assert info.converged
+        iters.append(int(info.iterations))
+        drift = max(drift, abs(s.energy().total - e0) / e0)
+    assert drift <= 1e-13, drift
+    assert max(iters[60:]) >= 2 * max(iters[:20]), iters      # the saturated regime
+    for _ in range(2):
+        check_accepted_step(s, oracle_level(s, q, m), ocfg, 1e-13)
     s.close()
 
 
