@@ -72,6 +72,8 @@ BYTES32_PER_PARTICLE = 52
 NCU_TRAFFIC = {
     ("k_push", "twostream-32c-2M"): (297.07e6, "ncu capture, one launch (dram read 259.32 MB + write 37.75 MB)"),
     ("k_push", "twostream-128c-134M"): (297.07e6 * 64, "the 32^3 capture scaled by particles (x 64)"),
+    ("k_push32", "twostream-32c-2M"): (96.43e6, "ncu capture, one launch (dram read 86.57 MB + write 9.86 MB)"),
+    ("k_push32", "twostream-128c-134M"): (96.43e6 * 64, "the 32^3 capture scaled by particles (x 64)"),
 }
 
 
@@ -450,7 +452,8 @@ def fp32_push_roofline(prof, workload, npart, hbm_gbs, hbm_note):
     bytes_per_launch = float(BYTES32_PER_PARTICLE) * npart
     gbs = bytes_per_launch * prof.push32_launches / (prof.push32_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
-            "traffic": NCU_TRAFFIC.get(("k_push32", workload), (None, None))[0], "peak_note": hbm_note,
+            "traffic": NCU_TRAFFIC.get(("k_push32", workload), (None, None))[0],
+            "traffic_source": NCU_TRAFFIC.get(("k_push32", workload), (None, "not captured"))[1], "peak_note": hbm_note,
             "kernel": "k_push32 (FP32 orbit push + next-orbit current scatter)",
             "bytes_per_particle_iteration": BYTES32_PER_PARTICLE, "launches": int(prof.push32_launches),
             "ms_per_launch": prof.push32_ms / prof.push32_launches,
