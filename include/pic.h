@@ -430,6 +430,8 @@ void pic_ensemble_destroy(pic_ensemble* e);
  * (dt^2 kappa^2 sigma / 2) src with a = kappa^2 dt^2 / 4 (src = rho_half for phi with sigma1,
  * J for A with sigma2), by the library's Chebyshev iteration (the fewest steps whose error
  * bound is below helmholtz_tol, at most 1024), then W^{n+1} = 2 (F^{n+1} - F^n) / dt - W^n.
+ * (pic_step solves the same system by FFT on 2^p 3^q meshes; the results agree to the
+ * solves' rounding.)
  *
  * Arguments: n, L: mesh nodes and box lengths (host); every array pointer is a DEVICE
  * pointer in the library's mesh layout (x-fastest; A, U, J component-major, 3 * ncell).

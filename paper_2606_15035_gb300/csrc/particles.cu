@@ -1184,9 +1184,18 @@ __global__ void k_sort_scatter(StepParams p, const int32_t* __restrict__ key, co
                                const int64_t* __restrict__ id, double* __restrict__ xi_d, double* __restrict__ v_d,
                                double* __restrict__ P_d, double* __restrict__ vprev_d, int64_t* __restrict__ id_d) {
     const int64_t np = p.np;
+    const int lane = threadIdx.x & 31;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t k = key[i];
-        int64_t pos = (int64_t)offset[k] + atomicAdd(cursor + k, 1);
+        const int32_t k = key[i];
+        // the lanes of a warp with the same cell take consecutive places with one atomic (the
+        // particles are nearly sorted already, so a warp holds one or two cells)
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, k);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (lane == leader) first = atomicAdd(cursor + k, __popc(peers));
+        first = __shfl_sync(peers, first, leader);
+        const int64_t pos = (int64_t)offset[k] + first + __popc(peers & ((1u << lane) - 1u));
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             xi_d[a * np + pos] = xi[a * np + i];

@@ -46,43 +46,56 @@ __device__ __forceinline__ int64_t line_base(int axis, int64_t l, const MeshDims
 // Stockham autosort: stage s of radix R, with L = product of the previous radices, takes
 // v_r = x[j + r n/R] (j < n/R, k = j mod L), twiddles v_r by exp(-+2 pi i k r / (L R)),
 // applies the radix-R DFT and stores output s at (j div L) L R + k + s L.
-__global__ void k_fft_axis(double2* __restrict__ data, MeshDims m, FftAxis ax, int inverse) {
+// A block transforms `lb` lines whose first elements are adjacent in memory (lines l0 .. l0 +
+// lb - 1 along y or z start at consecutive x, or consecutive x-y positions), so that the loads
+// and stores of a strided axis read lb consecutive complex values at a time; along x (stride 1)
+// lb is 1.  Shared memory holds the lb lines twice (ping-pong), line j at j n.
+__global__ void k_fft_axis(double2* __restrict__ data, MeshDims m, FftAxis ax, int inverse, int lb) {
     extern __shared__ double2 sbuf[];
     const int n = ax.n;
     const int64_t nlines = m.ncell / n;
+    const int64_t ngroups = nlines / lb;
     double2* field = data + (int64_t)blockIdx.y * m.ncell;
     const double sgn = inverse ? 1.0 : -1.0;
     const double s3 = sgn * 0.86602540378443864676;   // sin(2 pi / 3) with the transform's sign
-    for (int64_t l = blockIdx.x; l < nlines; l += gridDim.x) {
+    const int tot = lb * n;
+    for (int64_t gr = blockIdx.x; gr < ngroups; gr += gridDim.x) {
         double2* x = sbuf;
-        double2* y = sbuf + n;
-        double2* line = field + line_base(ax.axis, l, m);
-        for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = line[t * ax.stride];
+        double2* y = sbuf + tot;
+        double2* first = field + line_base(ax.axis, gr * lb, m);
+        // element t of line j sits at first + j + t stride (lb > 1 only where lines are adjacent)
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int j = e % lb, t = e / lb;
+            x[j * n + t] = lb > 1 ? first[j + (int64_t)t * ax.stride] : first[(int64_t)t * ax.stride];
+        }
         __syncthreads();
         int L = 1;
         for (int st = 0; st < ax.nst; ++st) {
             const int R = ax.radix[st];
             const int nb = n / R, tstep = n / (L * R);
-            for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            for (int e = threadIdx.x; e < lb * nb; e += blockDim.x) {
+                const int line = e / nb, j = e - line * nb;
+                const double2* xl = x + line * n;
+                double2* yl = y + line * n;
                 const int k = j % L;
                 const int out = (j / L) * L * R + k;
-                double2 v0 = x[j], v1 = x[j + nb];
+                double2 v0 = xl[j], v1 = xl[j + nb];
                 double2 t1 = ax.tw[k * tstep];
                 if (inverse) t1.y = -t1.y;
                 v1 = cmul(v1, t1);
                 if (R == 2) {
-                    y[out] = cadd(v0, v1);
-                    y[out + L] = csub(v0, v1);
+                    yl[out] = cadd(v0, v1);
+                    yl[out + L] = csub(v0, v1);
                 } else {
-                    double2 v2 = x[j + 2 * nb];
+                    double2 v2 = xl[j + 2 * nb];
                     double2 t2 = ax.tw[2 * k * tstep];
                     if (inverse) t2.y = -t2.y;
                     v2 = cmul(v2, t2);
                     const double2 sum = cadd(v1, v2), dif = csub(v1, v2);
                     const double2 mid = make_double2(v0.x - 0.5 * sum.x, v0.y - 0.5 * sum.y);
-                    y[out] = cadd(v0, sum);
-                    y[out + L] = make_double2(mid.x - s3 * dif.y, mid.y + s3 * dif.x);        // + i s3 dif
-                    y[out + 2 * L] = make_double2(mid.x + s3 * dif.y, mid.y - s3 * dif.x);    // - i s3 dif
+                    yl[out] = cadd(v0, sum);
+                    yl[out + L] = make_double2(mid.x - s3 * dif.y, mid.y + s3 * dif.x);        // + i s3 dif
+                    yl[out + 2 * L] = make_double2(mid.x + s3 * dif.y, mid.y - s3 * dif.x);    // - i s3 dif
                 }
             }
             __syncthreads();
@@ -91,7 +104,11 @@ __global__ void k_fft_axis(double2* __restrict__ data, MeshDims m, FftAxis ax, i
             y = t;
             L *= R;
         }
-        for (int t = threadIdx.x; t < n; t += blockDim.x) line[t * ax.stride] = x[t];
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int j = e % lb, t = e / lb;
+            if (lb > 1) first[j + (int64_t)t * ax.stride] = x[j * n + t];
+            else first[(int64_t)t * ax.stride] = x[j * n + t];
+        }
         __syncthreads();
     }
 }
@@ -351,10 +368,18 @@ void fft3(Ctx& c, double2* data, int nf, bool inverse) {
         const FftAxis ax = make_axis(c, a);
         if (ax.n == 1) continue;
         const int64_t nlines = c.m.ncell / ax.n;
-        int threads = std::min(256, std::max(32, ((ax.n / 2 + 31) / 32) * 32));
-        const int64_t gx = std::min<int64_t>(nlines, (int64_t)c.sms * 16);
+        // lines per block: 1 along x (contiguous); along y and z as many adjacent lines as keep
+        // the two shared copies within 32 KB and divide the run of adjacent line starts (the
+        // x extent for y, the x-y plane for z)
+        int lb = 1;
+        if (a > 0) {
+            const int64_t run = a == 1 ? c.m.n[0] : (int64_t)c.m.n[0] * c.m.n[1];
+            while (lb < 16 && 2 * (2 * lb) * ax.n <= 2048 && run % (2 * lb) == 0) lb *= 2;
+        }
+        int threads = std::min(256, std::max(32, ((lb * ax.n / 2 + 31) / 32) * 32));
+        const int64_t gx = std::min<int64_t>(nlines / lb, (int64_t)c.sms * 16);
         dim3 grid((unsigned)gx, (unsigned)nf);
-        k_fft_axis<<<grid, threads, 2 * ax.n * sizeof(double2), c.stream>>>(data, c.m, ax, inverse ? 1 : 0);
+        k_fft_axis<<<grid, threads, 2 * lb * ax.n * sizeof(double2), c.stream>>>(data, c.m, ax, inverse ? 1 : 0, lb);
         ++c.launches;
     }
 }
