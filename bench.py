@@ -414,7 +414,8 @@ def cpu_baseline(w):
 def kernel_shares(prof, ms):
     phases = {"k_push (FP64 iterations)": prof.push_ms, "k_push (FP64 final sweep)": prof.commit_ms,
               "k_local": prof.local_ms, "k_push32": prof.push32_ms, "mesh phases": prof.mesh_ms,
-              "first scatters": prof.scatter_ms, "sort": prof.sort_ms}
+              "first scatters": prof.scatter_ms, "sort": prof.sort_ms,
+              "k_push_df (FP32-pair iterations)": prof.pushpair_ms}
     return {k: v / ms for k, v in phases.items()} if ms > 0 else {}
 
 

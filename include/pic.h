@@ -135,9 +135,13 @@ typedef struct {
                                      next-orbit current) runs in FP32-pair arithmetic (two floats
                                      per value, a 48-bit significand, on the FP32 pipes) before the
                                      FP64 iterations; they stop early once e_v and e_J are <=
-                                     picard_tol or stop shrinking.  0 (default): none, FP64
-                                     refinement from the FP32 iterate.  Not used in deterministic
-                                     mode */
+                                     picard_tol or stop shrinking.  An FP32-pair iterate never ends
+                                     the step by Algorithm 1's test, but with mixed_tol64 > 0 it
+                                     can be tried as v* by the FP64 final sweep, which checks its
+                                     residual in FP64.  1 (default): one such iteration, which
+                                     replaces the FP64 iteration of the common step (the pair push
+                                     costs about 0.85 of the FP64 one at 128^3); 0: FP64 refinement
+                                     from the FP32 iterate.  Not used in deterministic mode */
 } pic_config;
 
 #define PIC_OPS_CENTRAL2 0
@@ -247,7 +251,7 @@ typedef struct {
 /* Fill cfg with defaults: 8^3 nodes, box 2 pi / 3, dt = 0.1, kappa = sigma1 = sigma2 = 1,
  * n0 = 1, tau = 1e-13, p_max = 16, split closed-form orbits, FP64, sort every step,
  * diagnostics off, local solves on, Chebyshev reduction 1e-17, mixed: FP32 phase to 1e-9,
- * at most 8 FP32 iterations, no FP32-pair refinement, FP64 refinement to picard_tol, not
+ * at most 8 FP32 iterations, one FP32-pair refinement iteration, FP64 refinement to picard_tol, not
  * deterministic, linear shapes (r = 1), central-difference operators. */
 pic_status pic_config_default(pic_config* cfg);
 

@@ -721,8 +721,9 @@ pic_status iter_finish(pic_ctx* ctx) {
         if (!std::isfinite(r.e_v) || (r.p > 0 && !std::isfinite(r.e_J)))
             return fail(ctx, PIC_ERR_NONFINITE, "pic_step: non-finite Picard residual");
         if (r.pair_issued) {
-            // An FP32-pair iteration never ends the step: the FP64 iterations that follow check
-            // the iterate in FP64.  The pair phase ends once its iterate meets picard_tol (its
+            // An FP32-pair iteration never ends the step by Algorithm 1's test: the FP64
+            // iterations that follow, or the FP64 final sweep of a trial, check the iterate in
+            // FP64.  The pair phase ends once its iterate meets picard_tol (its
             // fixed point is the FP64 one to ~1e-15 of the speed), stops shrinking, or has run
             // mixed_pair_max iterations.
             ++r.ppair;
@@ -738,14 +739,14 @@ pic_status iter_finish(pic_ctx* ctx) {
             r.iterating = false;
             return PIC_OK;
         }
-        // PIC_MIXED: the FP64 iterate v^{p+1} is tried as v* when its predicted residual is
-        // within mixed_tol64; the final sweep of the trial measures that residual and commits
-        // only if it is within (trial_issue).  The prediction: the residual left by an update is
+        // PIC_MIXED: the FP64 or FP32-pair iterate v^{p+1} is tried as v* when its predicted
+        // residual is within mixed_tol64; the FP64 final sweep of the trial measures that
+        // residual and commits only if it is within (trial_issue).  The prediction: the residual left by an update is
         // driven by the change of the current it made, so once a trial has measured the ratio
         // kappa = ||G(v*) - v*|| / e_J, 2 kappa e_J; before that, the contraction seen so far
         // (the FP32 phase's e_v[1] / e_v[0] after the first FP64 iteration, else the last two
         // FP64 e_v) times e_v.
-        if (!r.pair_issued && r.began32 && c.cfg.mixed_tol64 > 0.0 && !c.cfg.diagnostics) {
+        if (r.began32 && c.cfg.mixed_tol64 > 0.0 && !c.cfg.diagnostics) {
             double pred = INFINITY;
             if (c.trial_kappa > 0.0 && std::isfinite(r.e_J)) {
                 pred = 2.0 * c.trial_kappa * r.e_J;
@@ -923,7 +924,7 @@ pic_status pic_config_default(pic_config* cfg) {
     cfg->picard_accel = 1;
     cfg->mixed_tol32 = 1e-9;
     cfg->mixed_max32 = 8;
-    cfg->mixed_pair_max = 0;
+    cfg->mixed_pair_max = 1;
     cfg->deterministic = 0;
     cfg->shape_order = 1;
     cfg->ops = PIC_OPS_CENTRAL2;

@@ -241,12 +241,16 @@ def test_late_time_thermal_8c_steps_are_fixed_points(sim):
     s.close()
 
 
-def test_full_size_32c_steps_are_fixed_points(sim):
-    """The 32^3 x 2,097,152-particle workload (the benchmark's launch configuration), two
-    steps, each checked whole by one oracle evaluation of Algorithm 1's map."""
+@pytest.mark.parametrize("variant", ["fp64", "spectral", "mixed"])
+def test_full_size_32c_steps_are_fixed_points(sim, variant):
+    """The 32^3 x 2,097,152-particle workload, two steps, each checked whole by one oracle
+    evaluation of Algorithm 1's map: the FP64 path with central differences (its CN solves by
+    FFT plus refinement), the paper's spectral operators, and the mixed path (FP32 iterations,
+    FP64 refinement to tau)."""
     w = pi.WORKLOADS["twostream-32c-2M"]
     x, v, q, m = pi.workload_particles(w)
-    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_max=w.picard_max)
+    kw = {"spectral": dict(ops=1), "mixed": dict(precision=1)}.get(variant, {})
+    s, ocfg = make(sim, x, v, q, m, w.n, w.L, w.picard_tol, dt=w.dt, picard_max=w.picard_max, **kw)
     for _ in range(2):
         check_accepted_step(s, oracle_level(s, q, m), ocfg, w.picard_tol)
     s.close()
