@@ -17,9 +17,11 @@ max_n |E^n - E^0| / E^0 <= 1e-9; FP64 path drift <= 1e-12.  The map of Algorithm
 where an orbit endpoint crosses a knot, so a particle whose step lands within the paths'
 rounding difference of such a crossing may take a different (equally valid) root on the two
 paths; that is why the comparison is in L2, as the target states it, not element by element.  The mixed path is
-run twice: refining in FP64 to tau, and to the looser mixed_tol64 = 1e-10 that the
+run three times: refining in FP64 to tau, to mixed_tol64 = 1e-10, and to the 1e-9 that the
 benchmark uses (its energy error per step is the product of the velocity change and the
-fixed-point residual, second order, so the drift bound still holds)."""
+fixed-point residual, second order, so the drift bound still holds).  With mixed_tol64 > 0 the
+step's refinement is usually one FP32-pair iteration whose iterate the FP64 final sweep checks
+and commits."""
 
 import numpy as np
 import pytest
@@ -43,7 +45,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("mixed_tol64", [0.0, 1e-10])
+@pytest.mark.parametrize("mixed_tol64", [0.0, 1e-10, 1e-9])
 def test_mixed_path_tracks_fp64_path_on_the_128_mesh(sim, mixed_tol64):
     w = pi.WORKLOADS["twostream-128c-134M"]
     x, v, q, m = pi.random_twostream(w.n, w.L, 8, w.v0, w.eps, w.vth, w.seed)     # 16 per cell, 33.5M
