@@ -493,7 +493,7 @@ def pair_push_summary(prof, npart, step_ms):
     return {"kernel": "k_push_df (FP32-pair push + next-orbit current scatter)", "launches": int(prof.pushpair_launches),
             "ms_per_launch": ms_l, "share_of_step": prof.pushpair_ms / step_ms if step_ms > 0 else None,
             "fp64_equivalent_tflops": flops / (ms_l / 1e3) / 1e12,
-            "note": "FP32 pipes, two blocks per SM; the FP64 push's flop count for the same work, per launch time"}
+            "note": "FP32 pipes, four blocks per SM; the FP64 push's flop count for the same work, per launch time"}
 
 
 def fp32_push_roofline(prof, workload, npart, hbm_gbs, hbm_note):

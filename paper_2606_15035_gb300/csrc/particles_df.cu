@@ -202,7 +202,7 @@ __device__ __forceinline__ int scatter_df(const ParamsDF& pd, const TileDF& tl, 
 
 // The FP32-pair iteration: G(v^p) for every particle, creeping ones listed for k_local (as in
 // k_push), the e_v partial sums, and the orbit current of v^{p+1} = G(v^p) into Jnext.
-__global__ void __launch_bounds__(THREADS, 2) k_push_df(ParamsDF pd, const double* __restrict__ xi,
+__global__ void __launch_bounds__(THREADS, 4) k_push_df(ParamsDF pd, const double* __restrict__ xi,
                                                          const double* __restrict__ v, const double* __restrict__ P,
                                                          const double* __restrict__ vit,
                                                          const float4* __restrict__ table, double* __restrict__ vnew,
