@@ -378,7 +378,8 @@ __device__ __forceinline__ T particle_phi(const AdjParams& ap, const T x0[3], co
 
 // Per particle: the adjoints of the start position (lam_xi) and of v* (g = dt/(2H) dPhi/dbeta,
 // which is also the adjoint of v^n), and the block B = dG_i/dv*_i (9, row-major) of the
-// block-Jacobi solve.  lam_xe: adjoint of the end position x^{n+1} in cell units.
+// transposed solve's preconditioner (zero outside the particles the step solved locally).
+// lam_xe: adjoint of the end position x^{n+1} in cell units.
 __global__ void __launch_bounds__(THREADS) k_adj_derivs(AdjParams ap, const double* __restrict__ xi,
                                                         const double* __restrict__ v, const double* __restrict__ vstar,
                                                         const double* __restrict__ table, const double* __restrict__ lJ,

@@ -198,7 +198,7 @@ struct Ctx {
 
     // adjoint (pic_step_vjp / pic_init_vjp), allocated on first use: particles (3 np each) the
     // adjoints of x^{n+1} (cell units), v^{n+1}, P^{n+1}, of v* (two buffers), of x^n, the
-    // block-Jacobi right-hand side g and blocks B (9 np), a scratch; mesh: the gather table's
+    // sweep's adjoint of v* g and the preconditioner's blocks B (9 np), a scratch; mesh: the gather table's
     // adjoint (9 N), the level-(n+1) inputs and level-n outputs, the Helmholtz buffers, J's adjoint
     bool fresh_init = false;             // the state is pic_init's (no step or set_state since)
     double *adj_xe = nullptr, *adj_v = nullptr, *adj_P = nullptr, *adj_mu = nullptr, *adj_mu2 = nullptr;
