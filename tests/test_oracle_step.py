@@ -12,6 +12,11 @@
   growing eigenmode.
 * Planted mistakes: pushing with (D A) instead of (D A)^T must break energy
   conservation.
+* The energy error of a step closed from a non-converged iterate v* (the final sweep of §5.4
+  from v*): the field-energy balance and the orbit's power balance hold for the orbit of v*
+  whatever v* is, so R_total = (m/2) sum_i (v_i^{n+1} - v_i^n) . (G(v*)_i - v*_i), second order
+  in the step's velocity change and the fixed-point residual.  The mixed path's tolerance and
+  its final sweep's check of the accepted iterate's own residual rest on this identity.
 """
 
 import numpy as np
@@ -264,3 +269,30 @@ def test_stopping_on_one_updates_errors_is_accurate_to_tolerance():
         assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y), name
     E0 = sum(pic.energy(st, cfg))
     assert abs(ia["R_total"]) <= 1e-14 * E0
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1e-8, 1e-10])
+def test_energy_error_of_an_unconverged_iterate_is_the_residual_product(scale):
+    w = pi.WORKLOADS["twostream-8c-8k"]
+    x, v, q, m = pi.random_twostream((8, 8, 8), w.L, 4, w.v0, w.eps, 1e-2, 77)
+    cfg = pic.Config(n=(8, 8, 8), L=w.L, dt=w.dt, picard_tol=1e-14)
+    grid = cfg.grid()
+    st = pic.init(x, v, q, m, cfg)
+    for _ in range(3):
+        st, _ = pic.step(st, cfg)
+    conv, _ = pic.step(st, cfg)
+    K0, W0 = pic.energy(st, cfg)
+    E0 = K0 + W0
+    rng = np.random.default_rng(3)
+    vstar = conv.v + scale * np.abs(conv.v).max() * rng.normal(size=conv.v.shape)
+    it = pic.picard_iteration(st, vstar, cfg, grid)
+    K1 = 0.5 * m * np.sum(it["v_new"] ** 2)
+    W1 = mesh.field_energy(it["phi"], it["U"], it["A"], cfg.sigma1, cfg.sigma2, grid)
+    R = (K1 + W1) - E0
+    pred = 0.5 * m * np.sum((it["v_new"] - st.v) * (it["v_new"] - vstar))
+    assert abs(pred) > 1e3 * 1e-16 * E0 or scale == 1e-10     # a defect well above roundoff
+    assert abs(R - pred) <= 1e-15 * E0, (R / E0, pred / E0)
+    # and the identity's content: the defect is second order, |R| <= |dv| |G(v*) - v*| m / 2
+    bound = 0.5 * m * np.linalg.norm(it["v_new"] - st.v) * np.linalg.norm(it["v_new"] - vstar)
+    assert abs(R) <= bound * (1 + 1e-6) + 1e-15 * E0
+
