@@ -8,8 +8,11 @@
 // residual sums and the FP64 iterations that close the step use them unchanged.  The pair
 // map differs from the FP64 map G by ~1e-15 of the velocity (positions are carried as the
 // cell index plus a pair offset in the cell, so their resolution is 2^-48 cells at any mesh
-// size), so its fixed point is the FP64 fixed point to that level, and the FP64 iteration
-// that follows confirms it within the FP64 tolerance.
+// size), so its fixed point is the FP64 fixed point to that level.  What checks the iterate
+// is FP64: the FP64 final sweep, which measures ||G(v*) - v*|| of the pair iterate itself
+// before committing it (the mixed path's default with mixed_tol64 > 0), or the FP64
+// iterations that follow.  Compiled for four resident blocks per SM (64 registers, with
+// spills): the pair arithmetic's dependent chains need the warps more than the registers.
 //
 // Per chunk of THREADS cell-sorted particles the next-orbit current goes into a shared-memory
 // tile of 64-bit fixed-point sums (exact, order independent, 2^-52 of the chunk's largest
